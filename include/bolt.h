@@ -1,0 +1,187 @@
+/*
+ * bolt.h -- C ABI of the GB300 (sm_103a) Bolt library, libbolt.so.
+ *
+ * Bolt (Blalock & Guttag, "Bolt: Accelerated Data Mining with Fast Vector
+ * Compression", KDD'17) approximates a distance d(q, x) = f(sum_j delta(q_j,
+ * x_j)) (Sec. 1.1) by
+ *   h(x): M 4-bit codes, the nearest of K = 16 centroids per subspace
+ *         (Sec. 3.1 encoding function h; K = 16 from Sec. 3.2, change 1),
+ *   g(q): an M x 16 table of subvector-to-centroid distances quantized to
+ *         uint8 by beta_m(y) = clamp(floor(a (y - b_m)), 0, 255) (Sec. 3.2),
+ *   d^ :  the sum over m of the table entries the codes pick (Sec. 3.1,
+ *         approximate distance as a sum of table entries).
+ *
+ * Conventions for every entry point
+ *  - Array arguments are DEVICE pointers owned by the caller unless the
+ *    parameter name ends in _host.  The library never frees or keeps them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream unless stated.
+ *  - Every call returns BOLT_OK (0) or an error code; no exception crosses
+ *    the ABI.  bolt_last_error() returns this thread's last message.
+ *  - Sizes: n database vectors, J dims, M codebooks (J % M == 0,
+ *    1 <= M <= 256, s = J/M dims per subspace, subspace m owning dims
+ *    [m*s, (m+1)*s), Sec. 3.1 "consecutive indices"), nq queries.
+ *  - Dense float inputs are row-major fp32 (X: n x J, Q: nq x J).
+ *  - centroids: fp32 [M][16][s].
+ *  - Codes use the BLOCKED layout: vectors are grouped in blocks of 256; block
+ *    b stores M rows of 128 bytes, row m holding the 4-bit codes of codebook m
+ *    for vectors 256b .. 256b+255; within a row, little-endian 32-bit word w
+ *    holds vectors 256b + 8w + i in bits [4i, 4i+4), i = 0..7.  Vectors past
+ *    n in the last block are code 0 and never reported.  Size:
+ *    bolt_codes_bytes(n, M) = ceil(n/256) * M * 128 bytes (16-byte aligned
+ *    base required).
+ *  - luts: uint8 [nq][M][16] (16 contiguous entries per query and codebook).
+ *  - Scan sums are exact integers stored as uint16 (255*M <= 65280).
+ *  - Top-k order: L2 ascending sum, dot descending sum, ties to the lower
+ *    vector index; rows with k > n are padded with index -1 and sum 0.
+ */
+#ifndef BOLT_H_
+#define BOLT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BOLT_OK 0
+#define BOLT_EINVAL 1       /* bad pointer, shape, alignment or argument */
+#define BOLT_EUNSUPPORTED 2 /* J % M != 0, M > 256, k too large, ... */
+#define BOLT_ENOMEM 3       /* workspace too small or allocation failed */
+#define BOLT_ECUDA 4        /* a CUDA runtime call or launch failed */
+#define BOLT_ETIMEOUT 5     /* a bounded device wait gave up */
+
+#define BOLT_METRIC_L2 0  /* delta = squared difference, f = sqrt (Sec. 1.1) */
+#define BOLT_METRIC_DOT 1 /* delta = product, f = identity (Sec. 1.1) */
+
+#define BOLT_PREC_FP32 0         /* canonical fp32 encoder */
+#define BOLT_PREC_BF16_RECHECK 1 /* tensor-core bf16 scores + fp32 re-check */
+
+/* Thread-local message for the last failing call on this thread ("" if none).
+ * Valid until the next call on the same thread. */
+const char *bolt_last_error(void);
+
+/* Library version string. */
+const char *bolt_version(void);
+
+/* ---------------------------------------------------------------- layout
+ * Size in bytes of the blocked code array for n vectors and M codebooks
+ * (ceil(n/256) * M * 128); -1 for invalid arguments.  Host only. */
+int64_t bolt_codes_bytes(int64_t n, int32_t M);
+
+/* Convert row-major codes (n x M bytes, each 0..15) to the blocked layout.
+ * Codes are not range-checked on the device: only the low nibble of each
+ * byte is stored.  blocked: bolt_codes_bytes(n, M) bytes, fully written
+ * (padding codes are 0). */
+int bolt_pack_codes(const uint8_t *rowmajor, int64_t n, int32_t M,
+                    uint8_t *blocked, void *stream);
+
+/* Inverse of bolt_pack_codes: blocked -> row-major n x M bytes (0..15). */
+int bolt_unpack_codes(const uint8_t *blocked, int64_t n, int32_t M,
+                      uint8_t *rowmajor, void *stream);
+
+/* ---------------------------------------------------------------- encode h
+ * Sec. 3.1, h(x)_m = argmin_i d(c_i^(m), x^(m)) over K = 16 centroids.
+ * The canonical distance of (x, m, k) is the fp32 sum over the subspace's
+ * dims, in dim order, of acc = fmaf(t, t, acc), t = x_j - c_j, from 0; ties
+ * go to the lowest k.
+ * precision BOLT_PREC_FP32 computes exactly that.  BOLT_PREC_BF16_RECHECK
+ * scores ||c||^2 - 2 x.c on tcgen05 tensor cores in bf16 with fp32
+ * accumulation and re-evaluates the canonical fp32 distances of every
+ * centroid within a rigorous error margin of the best score, so its codes
+ * equal BOLT_PREC_FP32's.
+ * X: n x J fp32 (16-byte aligned); codes: blocked, bolt_codes_bytes(n, M).
+ * n_rechecked (nullable, device int64): set to the number of (vector,
+ * subspace) pairs that took the fp32 re-check (0 for BOLT_PREC_FP32). */
+int bolt_encode(const float *X, int64_t n, int32_t J, int32_t M,
+                const float *centroids, int32_t precision, uint8_t *codes,
+                int64_t *n_rechecked, void *stream);
+
+/* ---------------------------------------------------------------- LUT g
+ * Sec. 3.1 query encoding D_im = delta(q^(m), c_i^(m)), then Sec. 3.2
+ * quantization beta_m.  L2: fp32 acc = fmaf(t, t, acc), t = q_j - c_j; dot:
+ * acc = fmaf(q_j, c_j, acc), both in dim order from 0.  Quantization: t =
+ * (y - b_m) then t * a, two fp32 roundings, floor, clamp to [0, 255], NaN to
+ * 0.  a: scale (host value); b_host: M offsets in HOST memory.
+ * luts: nq x M x 16 uint8.  luts_f32 (nullable): the unquantized table
+ * nq x M x 16 fp32 ("Bolt No Quantize", Sec. 4.2). */
+int bolt_build_luts(const float *Q, int64_t nq, int32_t J, int32_t M,
+                    const float *centroids, int32_t metric, float a,
+                    const float *b_host, uint8_t *luts, float *luts_f32,
+                    void *stream);
+
+/* ---------------------------------------------------------------- scan d^
+ * Sec. 3.1 approximate distance: sums[q][i] = sum_m luts[q][m][code_m(x_i)],
+ * exact, as uint16.  sums: nq x n.  The two names compute the same integer
+ * sums; they differ only in how top-k and dequantization read them. */
+int bolt_scan_l2(const uint8_t *codes, int64_t n, int32_t M,
+                 const uint8_t *luts, int64_t nq, uint16_t *sums, void *stream);
+int bolt_scan_dot(const uint8_t *codes, int64_t n, int32_t M,
+                  const uint8_t *luts, int64_t nq, uint16_t *sums, void *stream);
+
+/* ---------------------------------------------------------------- top-k
+ * Fused scan + exact top-k (nearest neighbours for L2, maximum inner product
+ * for dot; Sec. 1.2 and Sec. 4.5 use these searches).  out_sums: nq x k
+ * uint16, out_idx: nq x k int64, best first.  1 <= k <= 1024.
+ * workspace: device scratch of at least bolt_topk_workspace_bytes(n, M, nq,
+ * k) bytes, 256-byte aligned, or NULL to let the library allocate and free
+ * it stream-ordered (cudaMallocAsync/cudaFreeAsync) inside the call.
+ * Calls sharing one workspace must not overlap on the GPU. */
+int64_t bolt_topk_workspace_bytes(int64_t n, int32_t M, int64_t nq, int32_t k);
+int bolt_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts,
+              int64_t nq, int32_t k, int32_t metric, uint16_t *out_sums,
+              int64_t *out_idx, void *workspace, int64_t workspace_bytes,
+              void *stream);
+
+/* ---------------------------------------------------------------- dequantize
+ * Sec. 3.2: the per-table reconstructions beta_m/a + b_m sum to
+ * S * (1/a) + sum_m b_m.  Host helper (fp64, no GPU): inv_a =
+ * (float)(1/(double)a), bias = (float)(sum_m (double)b_host[m]). */
+int bolt_dequant_params(float a, const float *b_host, int32_t M, float *inv_a_host,
+                        float *bias_host);
+
+/* out[i] = fp32(fp32((float)S[i] * inv_a) + bias), count values. */
+int bolt_dequantize(const uint16_t *S, int64_t count, float inv_a, float bias,
+                    float *out, void *stream);
+
+/* ---------------------------------------------------------------- matmul
+ * Sec. 4.4 approximate matrix product: rows of A are queries with dot
+ * tables, codesB is the encoded database; out[i][j] is the dequantized
+ * approximate A_i . B_j.  A: rows x J fp32, codesB: blocked (n vectors),
+ * out: rows x n fp32. */
+int bolt_approx_matmul(const float *A, int64_t rows, int32_t J,
+                       const uint8_t *codesB, int64_t n, int32_t M,
+                       const float *centroids, float a, const float *b_host,
+                       float *out, void *stream);
+
+/* ---------------------------------------------------------------- fit
+ * Offline phase (Sec. 1.3).  k-means (Sec. 3.1 background) with exactly
+ * `iters` Lloyd iterations: assignment by the canonical fp32 encoder, means
+ * accumulated in fp64 and rounded to fp32, an empty cluster keeps its
+ * centroid; init_rows_host: 16 row indices whose subvectors seed every
+ * codebook.  If Qtrain != NULL the quantizer for `metric` is fitted as in
+ * bolt_fit_quantizer.  Blocking: returns after the work is done.
+ * centroids: output M x 16 x s fp32 (device).  a_host, b_host: outputs
+ * (ignored when Qtrain is NULL). */
+int bolt_fit_codebooks(const float *X, int64_t n, int32_t J, int32_t M,
+                       int32_t iters, const int64_t *init_rows_host,
+                       const float *Qtrain, int64_t nqt, int32_t metric,
+                       float *centroids, float *a_host, float *b_host,
+                       void *stream);
+
+/* Sec. 3.2 quantizer fit over the tables of nqt training queries, in fp64 on
+ * the GPU: b_m = lower-rank empirical alpha-quantile of table m (entry
+ * floor(alpha*(16*nqt-1)) of the sorted table), a = 255 / (entry
+ * floor((1-alpha)*(16*nqt*M-1)) of the sorted pooled offsets y - b_m) (a = 1
+ * if that is <= 0); alpha in {0,.001,.002,.005,.01,.02,.05,.1} minimizing the
+ * mean squared reconstruction error, ties to the smaller alpha.  Outputs
+ * rounded to fp32.  alpha_idx_host (nullable).  Blocking. */
+int bolt_fit_quantizer(const float *Qtrain, int64_t nqt, int32_t J, int32_t M,
+                       const float *centroids, int32_t metric, float *a_host,
+                       float *b_host, int32_t *alpha_idx_host, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BOLT_H_ */

@@ -1,0 +1,286 @@
+"""Thin Python binding of libbolt.so (the C ABI in include/bolt.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Tensors are torch CUDA tensors (torch supplies device memory and the
+current stream); functions with the same names as the C entry points (minus
+the ``bolt_`` prefix) allocate outputs when none are given.  There is no CPU
+fallback: if the library cannot be loaded, or no CUDA device is present,
+calls raise ``BoltError``.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbolt.so")
+
+OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, ETIMEOUT = range(6)
+METRIC_L2, METRIC_DOT = 0, 1
+PREC_FP32, PREC_BF16_RECHECK = 0, 1
+K = 16
+BLOCK = 256
+
+
+class BoltError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("bolt error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+_SIGS = {
+    "bolt_last_error": ([], C.c_char_p),
+    "bolt_version": ([], C.c_char_p),
+    "bolt_codes_bytes": ([C.c_int64, C.c_int32], C.c_int64),
+    "bolt_pack_codes": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_unpack_codes": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_encode": ([C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                     C.c_void_p], C.c_int),
+    "bolt_build_luts": ([C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_float,
+                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_scan_l2": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_scan_dot": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_topk_workspace_bytes": ([C.c_int64, C.c_int32, C.c_int64, C.c_int32], C.c_int64),
+    "bolt_topk": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
+                   C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
+    "bolt_dequant_params": ([C.c_float, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_dequantize": ([C.c_void_p, C.c_int64, C.c_float, C.c_float, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_approx_matmul": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                            C.c_float, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_fit_codebooks": ([C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                            C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_fit_quantizer": ([C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                            C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+}
+
+
+def lib():
+    """Load libbolt.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        from . import build as _build
+
+        if not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise BoltError(ECUDA, "libbolt.so is not built")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc):
+    if rc != OK:
+        raise BoltError(rc, lib().bolt_last_error().decode())
+
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise BoltError(ECUDA, "no CUDA device: the Bolt library has no CPU path")
+    return torch
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise BoltError(EINVAL, "%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise BoltError(EINVAL, "%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise BoltError(EINVAL, "%s must be contiguous" % name)
+    return t
+
+
+def _host_f32(b):
+    arr = np.ascontiguousarray(np.asarray(b, dtype=np.float32))
+    return arr, arr.ctypes.data_as(C.c_void_p)
+
+
+# ------------------------------------------------------------------ layout
+def codes_bytes(n, M):
+    return int(lib().bolt_codes_bytes(n, M))
+
+
+def pack_codes(rowmajor, out=None, stream=None):
+    torch = _torch()
+    _dev(rowmajor, torch.uint8, "rowmajor")
+    n, M = rowmajor.shape
+    if out is None:
+        out = torch.empty(codes_bytes(n, M), dtype=torch.uint8, device=rowmajor.device)
+    _check(lib().bolt_pack_codes(_ptr(rowmajor), n, M, _ptr(out), _stream(stream)))
+    return out
+
+
+def unpack_codes(blocked, n, M, out=None, stream=None):
+    torch = _torch()
+    _dev(blocked, torch.uint8, "blocked")
+    if out is None:
+        out = torch.empty((n, M), dtype=torch.uint8, device=blocked.device)
+    _check(lib().bolt_unpack_codes(_ptr(blocked), n, M, _ptr(out), _stream(stream)))
+    return out
+
+
+# ------------------------------------------------------------------ encode
+def encode(X, centroids, precision=PREC_FP32, out=None, n_rechecked=None, stream=None):
+    torch = _torch()
+    _dev(X, torch.float32, "X")
+    _dev(centroids, torch.float32, "centroids")
+    n, J = X.shape
+    M = centroids.shape[0]
+    if out is None:
+        out = torch.empty(codes_bytes(n, M), dtype=torch.uint8, device=X.device)
+    _check(lib().bolt_encode(_ptr(X), n, J, M, _ptr(centroids), precision, _ptr(out), _ptr(n_rechecked),
+                             _stream(stream)))
+    return out
+
+
+# ------------------------------------------------------------------ LUT
+def build_luts(Q, centroids, metric, a, b, out=None, out_f32=False, stream=None):
+    """Returns uint8 tables (nq, M, 16) [and fp32 tables if out_f32]."""
+    torch = _torch()
+    _dev(Q, torch.float32, "Q")
+    _dev(centroids, torch.float32, "centroids")
+    nq, J = Q.shape
+    M = centroids.shape[0]
+    if out is None:
+        out = torch.empty((nq, M, K), dtype=torch.uint8, device=Q.device)
+    f32 = torch.empty((nq, M, K), dtype=torch.float32, device=Q.device) if out_f32 else None
+    bh, bp = _host_f32(b)
+    _check(lib().bolt_build_luts(_ptr(Q), nq, J, M, _ptr(centroids), metric, float(a), bp, _ptr(out), _ptr(f32),
+                                 _stream(stream)))
+    return (out, f32) if out_f32 else out
+
+
+# ------------------------------------------------------------------ scan / top-k
+def _scan(fn, codes, n, M, luts, out, stream):
+    torch = _torch()
+    _dev(codes, torch.uint8, "codes")
+    _dev(luts, torch.uint8, "luts")
+    nq = luts.shape[0]
+    if out is None:
+        out = torch.empty((nq, n), dtype=torch.uint16, device=luts.device)
+    _check(fn(_ptr(codes), n, M, _ptr(luts), nq, _ptr(out), _stream(stream)))
+    return out
+
+
+def scan_l2(codes, n, M, luts, out=None, stream=None):
+    return _scan(lib().bolt_scan_l2, codes, n, M, luts, out, stream)
+
+
+def scan_dot(codes, n, M, luts, out=None, stream=None):
+    return _scan(lib().bolt_scan_dot, codes, n, M, luts, out, stream)
+
+
+def topk_workspace_bytes(n, M, nq, k):
+    v = int(lib().bolt_topk_workspace_bytes(n, M, nq, k))
+    if v < 0:
+        raise BoltError(EINVAL, lib().bolt_last_error().decode())
+    return v
+
+
+def topk(codes, n, M, luts, k, metric, out_sums=None, out_idx=None, workspace=None, stream=None):
+    """(sums uint16 (nq, k), idx int64 (nq, k)), best first."""
+    torch = _torch()
+    _dev(codes, torch.uint8, "codes")
+    _dev(luts, torch.uint8, "luts")
+    nq = luts.shape[0]
+    dev = luts.device
+    if out_sums is None:
+        out_sums = torch.empty((nq, k), dtype=torch.uint16, device=dev)
+    if out_idx is None:
+        out_idx = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    wbytes = workspace.numel() if workspace is not None else 0
+    _check(lib().bolt_topk(_ptr(codes), n, M, _ptr(luts), nq, k, metric, _ptr(out_sums), _ptr(out_idx),
+                           _ptr(workspace), wbytes, _stream(stream)))
+    return out_sums, out_idx
+
+
+# ------------------------------------------------------------------ dequantize / matmul
+def dequant_params(a, b):
+    bh, bp = _host_f32(b)
+    ia, bias = C.c_float(), C.c_float()
+    _check(lib().bolt_dequant_params(float(a), bp, bh.shape[0], C.byref(ia), C.byref(bias)))
+    return ia.value, bias.value
+
+
+def dequantize(S, a, b, out=None, stream=None):
+    torch = _torch()
+    _dev(S, torch.uint16, "S")
+    inv_a, bias = dequant_params(a, b)
+    if out is None:
+        out = torch.empty(S.shape, dtype=torch.float32, device=S.device)
+    _check(lib().bolt_dequantize(_ptr(S), S.numel(), inv_a, bias, _ptr(out), _stream(stream)))
+    return out
+
+
+def approx_matmul(A, codesB, n, centroids, a, b, out=None, stream=None):
+    torch = _torch()
+    _dev(A, torch.float32, "A")
+    _dev(codesB, torch.uint8, "codesB")
+    _dev(centroids, torch.float32, "centroids")
+    rows, J = A.shape
+    M = centroids.shape[0]
+    if out is None:
+        out = torch.empty((rows, n), dtype=torch.float32, device=A.device)
+    bh, bp = _host_f32(b)
+    _check(lib().bolt_approx_matmul(_ptr(A), rows, J, _ptr(codesB), n, M, _ptr(centroids), float(a), bp,
+                                    _ptr(out), _stream(stream)))
+    return out
+
+
+# ------------------------------------------------------------------ fit
+def fit_codebooks(X, M, iters, init_rows, Qtrain=None, metric=METRIC_L2, stream=None):
+    """Returns centroids (M, 16, J/M) and, with Qtrain, (a, b)."""
+    torch = _torch()
+    _dev(X, torch.float32, "X")
+    n, J = X.shape
+    cent = torch.empty((M, K, J // M), dtype=torch.float32, device=X.device)
+    rows = np.ascontiguousarray(init_rows, dtype=np.int64)
+    a = C.c_float(0.0)
+    b = np.zeros(M, np.float32)
+    nqt = 0 if Qtrain is None else Qtrain.shape[0]
+    if Qtrain is not None:
+        _dev(Qtrain, torch.float32, "Qtrain")
+    _check(lib().bolt_fit_codebooks(_ptr(X), n, J, M, iters, rows.ctypes.data_as(C.c_void_p), _ptr(Qtrain), nqt,
+                                    metric, _ptr(cent), C.byref(a), b.ctypes.data_as(C.c_void_p),
+                                    _stream(stream)))
+    if Qtrain is None:
+        return cent
+    return cent, np.float32(a.value), b
+
+
+def fit_quantizer(Qtrain, centroids, metric, stream=None):
+    """Returns (a, b[M], alpha_index)."""
+    torch = _torch()
+    _dev(Qtrain, torch.float32, "Qtrain")
+    _dev(centroids, torch.float32, "centroids")
+    nqt, J = Qtrain.shape
+    M = centroids.shape[0]
+    a = C.c_float(0.0)
+    b = np.zeros(M, np.float32)
+    ai = C.c_int32(0)
+    _check(lib().bolt_fit_quantizer(_ptr(Qtrain), nqt, J, M, _ptr(centroids), metric, C.byref(a),
+                                    b.ctypes.data_as(C.c_void_p), C.byref(ai), _stream(stream)))
+    return np.float32(a.value), b, int(ai.value)

@@ -1,0 +1,83 @@
+// Query encoding g (Sec. 3.1, D_im = delta(q^(m), c_i^(m))) and Bolt's
+// learned 8-bit quantization of the table (Sec. 3.2, beta_m).
+#include "lut.cuh"
+
+namespace bolt {
+
+// Canonical fp32 table entry.  L2: acc = fma(t, t, acc), t = q_j - c_j;
+// dot: acc = fma(q_j, c_j, acc); dims in order, starting from 0.
+__device__ __forceinline__ float lut_entry(const float *__restrict__ q, const float *__restrict__ c, int s,
+                                           int metric) {
+    float acc = 0.0f;
+    if (metric == BOLT_METRIC_L2) {
+        for (int j = 0; j < s; ++j) {
+            const float t = __fsub_rn(q[j], c[j]);
+            acc = __fmaf_rn(t, t, acc);
+        }
+    } else {
+        for (int j = 0; j < s; ++j) acc = __fmaf_rn(q[j], c[j], acc);
+    }
+    return acc;
+}
+
+// beta_m(y) = clamp(floor(a (y - b_m)), 0, 255): (y - b_m) and the product by
+// a are separately rounded fp32 operations; NaN maps to 0.
+__device__ __forceinline__ uint8_t quantize_entry(float y, float a, float b) {
+    float t = __fsub_rn(y, b);
+    t = __fmul_rn(t, a);
+    if (!(t >= 0.0f)) return 0;
+    if (t >= 255.0f) return 255;
+    return (uint8_t)floorf(t);
+}
+
+__global__ void build_luts_kernel(const float *__restrict__ Q, int64_t nq, int32_t J, int32_t M,
+                                  const float *__restrict__ C, int32_t metric, QuantParams qp,
+                                  uint8_t *__restrict__ luts, float *__restrict__ luts_f32) {
+    const int s = J / M;
+    const int64_t total = nq * M * kK;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t % kK);
+        const int m = (int)((t / kK) % M);
+        const int64_t q = t / ((int64_t)kK * M);
+        const float y = lut_entry(Q + q * J + m * s, C + ((int64_t)m * kK + k) * s, s, metric);
+        if (luts_f32) luts_f32[t] = y;
+        luts[t] = quantize_entry(y, qp.a, qp.b[m]);
+    }
+}
+
+int launch_build_luts(const float *Q, int64_t nq, int32_t J, int32_t M, const float *C, int32_t metric,
+                      const QuantParams &qp, uint8_t *luts, float *luts_f32, cudaStream_t stream) {
+    const int64_t total = nq * M * kK;
+    if (total == 0) return BOLT_OK;
+    int64_t grid = (total + 255) / 256;
+    const int64_t cap = (int64_t)device_sm_count() * 32;
+    if (cap > 0 && grid > cap) grid = cap;
+    build_luts_kernel<<<(int)grid, 256, 0, stream>>>(Q, nq, J, M, C, metric, qp, luts, luts_f32);
+    return check_launch("build_luts_kernel");
+}
+
+int make_quant_params(float a, const float *b_host, int32_t M, QuantParams *qp) {
+    BOLT_REQUIRE(b_host, BOLT_EINVAL, "b_host is null");
+    BOLT_REQUIRE(M >= 1 && M <= 256, BOLT_EUNSUPPORTED, "M=%d out of range", M);
+    qp->a = a;
+    for (int m = 0; m < 256; ++m) qp->b[m] = m < M ? b_host[m] : 0.0f;
+    return BOLT_OK;
+}
+
+}  // namespace bolt
+
+extern "C" int bolt_build_luts(const float *Q, int64_t nq, int32_t J, int32_t M, const float *centroids,
+                               int32_t metric, float a, const float *b_host, uint8_t *luts, float *luts_f32,
+                               void *stream) {
+    bolt::clear_error();
+    int rc = bolt::check_jm(J, M);
+    if (rc) return rc;
+    BOLT_REQUIRE(nq >= 0, BOLT_EINVAL, "nq=%lld < 0", (long long)nq);
+    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT, BOLT_EINVAL, "bad metric %d", metric);
+    BOLT_REQUIRE(nq == 0 || (Q && centroids && luts), BOLT_EINVAL, "null pointer");
+    bolt::QuantParams qp;
+    rc = bolt::make_quant_params(a, b_host, M, &qp);
+    if (rc) return rc;
+    return bolt::launch_build_luts(Q, nq, J, M, centroids, metric, qp, luts, luts_f32, (cudaStream_t)stream);
+}

@@ -1,0 +1,81 @@
+"""Host-only checks of the C ABI: the library builds, loads and exports
+every entry point include/bolt.h declares; host-side helpers and argument
+validation work without a GPU (no kernel is launched here)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1706_10283_gb300 import bolt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "bolt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bolt_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = bolt.lib()
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(L, name), name
+        assert name in bolt.exported_symbols(), name
+    assert b"sm_103a" in L.bolt_version()
+
+
+def test_codes_bytes_layout_arithmetic():
+    # ceil(n/256) blocks of M rows of 128 bytes
+    assert bolt.codes_bytes(0, 16) == 0
+    assert bolt.codes_bytes(1, 16) == 16 * 128
+    assert bolt.codes_bytes(256, 8) == 8 * 128
+    assert bolt.codes_bytes(257, 8) == 2 * 8 * 128
+    assert bolt.codes_bytes(1_000_000, 16) == 3907 * 16 * 128
+    # M/2 bytes per vector once blocks are full (the paper's 8B/16B/32B codes)
+    for M, nbytes in ((16, 8), (32, 16), (64, 32)):
+        assert bolt.codes_bytes(256 * 1000, M) == 256 * 1000 * nbytes
+    assert bolt.lib().bolt_codes_bytes(-1, 4) == -1
+    assert bolt.lib().bolt_codes_bytes(10, 257) == -1
+
+
+def test_dequant_params_match_oracle():
+    rng = np.random.default_rng(0)
+    for M in (1, 8, 32, 256):
+        a = np.float32(rng.uniform(0.01, 10))
+        b = rng.standard_normal(M).astype(np.float32) * 100
+        assert bolt.dequant_params(a, b) == tuple(float(v) for v in oracle.dequant_params(a, b))
+
+
+def test_invalid_arguments_are_rejected_on_host():
+    L = bolt.lib()
+    nul = C.c_void_p(0)
+    # J not a multiple of M
+    rc = L.bolt_encode(nul, 10, 30, 8, nul, 0, nul, nul, nul)
+    assert rc == bolt.EUNSUPPORTED and b"multiple" in L.bolt_last_error()
+    # M > 256
+    assert L.bolt_scan_l2(nul, 10, 300, nul, 1, nul, nul) == bolt.EUNSUPPORTED
+    # bad metric
+    assert L.bolt_build_luts(nul, 1, 8, 2, nul, 7, C.c_float(1.0), nul, nul, nul, nul) == bolt.EINVAL
+    # k out of range
+    assert L.bolt_topk_workspace_bytes(100, 8, 1, 0) == -1
+    assert L.bolt_topk_workspace_bytes(100, 8, 1, 5000) == -1
+    # non-positive scale
+    ia, bb = C.c_float(), C.c_float()
+    arr = np.zeros(4, np.float32)
+    assert L.bolt_dequant_params(C.c_float(0.0), arr.ctypes.data_as(C.c_void_p), 4, C.byref(ia), C.byref(bb)) \
+        == bolt.EINVAL
+
+
+def test_binding_fails_loudly_without_cuda():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(bolt.BoltError):
+        bolt.encode(torch.zeros(4, 8), torch.zeros(2, 16, 4))

@@ -1,0 +1,298 @@
+"""GPU parity: every stage of the CUDA path against the CPU oracle on the
+same seeded inputs.  Integer outputs (codes, table bytes, sums, top-k) must be
+bit-exact; float outputs use the canonical fp32 order on both sides and are
+compared bit-exact too, with the fp64 oracle as a 1e-5 relative check.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1706_10283_gb300 import bolt, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    bolt.lib()
+    return torch
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def decode_blocked(buf, n, M):
+    """Independent numpy reading of the blocked layout in include/bolt.h."""
+    nb = (n + 255) // 256
+    words = np.frombuffer(buf.tobytes(), dtype="<u4").reshape(nb, M, 32)
+    nib = (words[..., None] >> (4 * np.arange(8, dtype=np.uint32))) & 15  # (nb, M, 32, 8)
+    return nib.transpose(0, 2, 3, 1).reshape(nb * 256, M)[:n].astype(np.uint8)
+
+
+def problem(n, J, M, seed, kind="mixture", nq=5):
+    X = synth.mixture(n, J, seed) if kind == "mixture" else synth.iid(n, J, seed)
+    Q = synth.mixture(nq, J, seed + 100) if kind == "mixture" else synth.iid(nq, J, seed + 100)
+    nfit = min(n, 4000)
+    if nfit >= 16:
+        C_ = oracle.kmeans(X[:nfit], M, 4, synth.kmeans_init_rows(nfit, seed))
+    else:  # too few rows to seed 16 centroids: random codebooks
+        C_ = synth.iid(M * 16, J // M, seed + 7).reshape(M, 16, J // M)
+    return X, Q, C_
+
+
+SHAPES = [(10_000, 32, 8, "iid"), (1_037, 128, 16, "mixture"), (513, 24, 4, "mixture"), (300, 64, 64, "mixture"),
+          (257, 16, 1, "mixture"), (40, 256, 32, "mixture"), (5, 8, 2, "iid")]
+
+
+# ------------------------------------------------------------------ layout
+def test_pack_unpack_roundtrip(torch_cuda):
+    torch = torch_cuda
+    rng = np.random.default_rng(0)
+    for n, M in ((1, 1), (255, 3), (256, 16), (1000, 32), (70_001, 8)):
+        codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+        blocked = bolt.pack_codes(dev(torch, codes))
+        assert blocked.numel() == bolt.codes_bytes(n, M)
+        np.testing.assert_array_equal(decode_blocked(blocked.cpu().numpy(), n, M), codes)
+        # padding codes are zero
+        tail = decode_blocked(blocked.cpu().numpy(), ((n + 255) // 256) * 256, M)[n:]
+        assert not tail.any()
+        np.testing.assert_array_equal(bolt.unpack_codes(blocked, n, M).cpu().numpy(), codes)
+
+
+# ------------------------------------------------------------------ encoder
+@pytest.mark.parametrize("n,J,M,kind", SHAPES)
+def test_encode_fp32_bitexact(torch_cuda, n, J, M, kind):
+    torch = torch_cuda
+    X, _, C_ = problem(n, J, M, 1, kind)
+    got = bolt.encode(dev(torch, X), dev(torch, C_), bolt.PREC_FP32)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(decode_blocked(got.cpu().numpy(), n, M), oracle.encode(X, C_))
+
+
+def test_encode_adversarial_ties(torch_cuda):
+    """Exact ties (duplicated centroids, points on centroids) resolve to the
+    lower index on both sides."""
+    torch = torch_cuda
+    rng = np.random.default_rng(5)
+    C_ = rng.integers(-4, 4, (4, 16, 4)).astype(np.float32)
+    C_[:, 9] = C_[:, 3]
+    pick = rng.integers(0, 16, (3000, 4))
+    X = np.concatenate([C_[m, pick[:, m]] for m in range(4)], axis=1)
+    X[::7] += np.float32(0.5)  # half-way points between integer centroids
+    got = bolt.encode(dev(torch, X), dev(torch, C_))
+    np.testing.assert_array_equal(decode_blocked(got.cpu().numpy(), len(X), 4), oracle.encode(X, C_))
+
+
+# ------------------------------------------------------------------ LUT
+@pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
+@pytest.mark.parametrize("n,J,M,kind", SHAPES[:5])
+def test_luts_bitexact(torch_cuda, metric, n, J, M, kind):
+    torch = torch_cuda
+    X, Q, C_ = problem(n, J, M, 2, kind, nq=37)
+    Dtr = oracle.lut_f32(X[:256], C_, metric)
+    a, b, _, _ = oracle.fit_quant(Dtr)
+    luts, f32 = bolt.build_luts(dev(torch, Q), dev(torch, C_), metric, a, b, out_f32=True)
+    D = oracle.lut_f32(Q, C_, metric)
+    np.testing.assert_array_equal(f32.cpu().numpy(), D)
+    np.testing.assert_array_equal(luts.cpu().numpy(), oracle.quantize(D, a, b))
+    D64 = oracle.lut_f64(Q, C_, metric)
+    # 1e-5 relative to the magnitude of the terms summed (|q||c| scale)
+    scale = np.abs(D64) if metric == bolt.METRIC_L2 else (
+        np.abs(Q).reshape(37, M, 1, -1) * np.abs(C_)[None]).sum(-1)
+    assert np.all(np.abs(f32.cpu().numpy() - D64) <= 1e-5 * np.maximum(scale, 1e-30))
+
+
+# ------------------------------------------------------------------ scan
+@pytest.mark.parametrize("n,M", [(1, 1), (300, 3), (4096, 16), (10_007, 8), (70_000, 32), (1000, 256)])
+def test_scan_sums_bitexact(torch_cuda, n, M):
+    torch = torch_cuda
+    rng = np.random.default_rng(n + M)
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+    luts = rng.integers(0, 256, (3, M, 16)).astype(np.uint8)
+    blocked = bolt.pack_codes(dev(torch, codes))
+    ref = oracle.scan(codes, luts)
+    for fn in (bolt.scan_l2, bolt.scan_dot):
+        got = fn(blocked, n, M, dev(torch, luts))
+        np.testing.assert_array_equal(got.cpu().numpy(), ref)
+
+
+def test_scan_extreme_tables(torch_cuda):
+    """All-255 tables at M = 256 reach the largest sum 65280; all-zero give 0."""
+    torch = torch_cuda
+    n, M = 777, 256
+    codes = np.random.default_rng(1).integers(0, 16, (n, M)).astype(np.uint8)
+    luts = np.stack([np.full((M, 16), 255, np.uint8), np.zeros((M, 16), np.uint8)])
+    got = bolt.scan_l2(bolt.pack_codes(dev(torch, codes)), n, M, dev(torch, luts)).cpu().numpy()
+    assert np.all(got[0] == 65280) and np.all(got[1] == 0)
+
+
+# ------------------------------------------------------------------ top-k
+def check_topk(torch, codes, luts, k, metric, workspace=None):
+    n, M = codes.shape
+    blocked = bolt.pack_codes(dev(torch, codes))
+    s, i = bolt.topk(blocked, n, M, dev(torch, luts), k, metric, workspace=workspace)
+    rs, ri = oracle.topk(oracle.scan(codes, luts), k, metric)
+    np.testing.assert_array_equal(i.cpu().numpy(), ri)
+    np.testing.assert_array_equal(s.cpu().numpy(), rs)
+
+
+@pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
+@pytest.mark.parametrize("n,M,k", [(5, 4, 10), (256, 8, 1), (1000, 8, 10), (10_003, 16, 100), (70_000, 16, 37),
+                                   (200_000, 8, 100), (50_000, 32, 1000), (20_000, 64, 50), (3000, 128, 20),
+                                   (600, 256, 5)])
+def test_topk_bitexact(torch_cuda, metric, n, M, k):
+    rng = np.random.default_rng(n * 7 + M + k + metric)
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+    luts = rng.integers(0, 256, (3, M, 16)).astype(np.uint8)
+    check_topk(torch_cuda, codes, luts, k, metric)
+
+
+@pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
+def test_topk_heavy_ties(torch_cuda, metric):
+    """Tables with 2 distinct values: huge tie groups decided by index."""
+    rng = np.random.default_rng(3)
+    n, M = 100_000, 8
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+    luts = rng.integers(0, 2, (2, M, 16)).astype(np.uint8)
+    check_topk(torch_cuda, codes, luts, 100, metric)
+    luts0 = np.zeros((1, M, 16), np.uint8)  # every sum equal
+    check_topk(torch_cuda, codes, luts0, 64, metric)
+
+
+def test_topk_sorted_input_worst_case(torch_cuda):
+    """Sums decreasing with the index: every block improves the threshold."""
+    torch = torch_cuda
+    n, M = 60_000, 16
+    codes = np.zeros((n, M), np.uint8)
+    val = (15 - (np.arange(n) * 16 // n)).astype(np.uint8)
+    codes[:, :] = val[:, None]
+    luts = np.tile(np.arange(16, dtype=np.uint8) * 16, (1, M, 1))
+    check_topk(torch, codes, luts, 100, bolt.METRIC_L2)
+
+
+def test_topk_explicit_workspace(torch_cuda):
+    torch = torch_cuda
+    rng = np.random.default_rng(4)
+    n, M, k = 30_000, 16, 50
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+    luts = rng.integers(0, 256, (4, M, 16)).astype(np.uint8)
+    ws = torch.empty(bolt.topk_workspace_bytes(n, M, 4, k), dtype=torch.uint8, device="cuda")
+    for _ in range(2):  # reuse of one workspace
+        check_topk(torch, codes, luts, k, bolt.METRIC_L2, workspace=ws)
+    with pytest.raises(bolt.BoltError):
+        small = torch.empty(16, dtype=torch.uint8, device="cuda")
+        blocked = bolt.pack_codes(dev(torch, codes))
+        bolt.topk(blocked, n, M, dev(torch, luts), k, bolt.METRIC_L2, workspace=small)
+
+
+# ------------------------------------------------------------------ dequantize / matmul
+def test_dequantize_bitexact(torch_cuda):
+    torch = torch_cuda
+    rng = np.random.default_rng(6)
+    S = rng.integers(0, 65281, 10_001).astype(np.uint16)
+    a, b = np.float32(0.37), rng.standard_normal(16).astype(np.float32)
+    got = bolt.dequantize(dev(torch, S), a, b).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle.dequant(S, a, b))
+
+
+@pytest.mark.parametrize("rows,n,J,M", [(37, 1000, 64, 8), (8, 257, 32, 32), (100, 5000, 128, 16)])
+def test_approx_matmul_bitexact(torch_cuda, rows, n, J, M):
+    torch = torch_cuda
+    B = synth.mixture(n, J, 0)
+    A = synth.iid(rows, J, 9)
+    C_ = oracle.kmeans(B, M, 4, synth.kmeans_init_rows(n, 0))
+    a, b, _, _ = oracle.fit_quant(oracle.lut_f32(A, C_, oracle.METRIC_DOT))
+    codes = oracle.encode(B, C_)
+    blocked = bolt.pack_codes(dev(torch, codes))
+    got = bolt.approx_matmul(dev(torch, A), blocked, n, dev(torch, C_), a, b).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle.matmul(A, codes, C_, a, b))
+
+
+# ------------------------------------------------------------------ fit
+@pytest.mark.parametrize("n,J,M,iters", [(5000, 32, 8, 8), (3000, 64, 16, 5), (10_000, 16, 1, 6)])
+def test_kmeans_matches_oracle(torch_cuda, n, J, M, iters):
+    torch = torch_cuda
+    X = synth.mixture(n, J, 3)
+    rows = synth.kmeans_init_rows(n, 3)
+    got = bolt.fit_codebooks(dev(torch, X), M, iters, rows).cpu().numpy()
+    ref, obj = oracle.kmeans(X, M, iters, rows, return_objective=True)
+    # fp64 means summed in a different (fixed) order: equal up to the last bit
+    np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-6)
+    codes_g = oracle.encode(X, got)
+    xh = oracle.decode(codes_g, got).astype(np.float64)
+    obj_g = ((X.astype(np.float64) - xh) ** 2).sum()
+    assert abs(obj_g - obj[-1]) <= 1e-5 * obj[-1]
+
+
+@pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
+def test_fit_quantizer_matches_oracle(torch_cuda, metric):
+    torch = torch_cuda
+    X, Q, C_ = problem(3000, 64, 8, 7)
+    Qtr = X[synth.train_query_rows(len(X), 7)]
+    a, b, ai = bolt.fit_quantizer(dev(torch, Qtr), dev(torch, C_), metric)
+    ra, rb, rai, _ = oracle.fit_quant(oracle.lut_f32(Qtr, C_, metric))
+    assert ai == rai
+    assert a == ra
+    np.testing.assert_array_equal(b, rb)
+
+
+# ------------------------------------------------------------------ workloads
+def test_small_iid_workload_end_to_end(torch_cuda):
+    """10,000 x 32 i.i.d. N(0,1), M = 8, 16 queries, top-10 (L2): fit, encode,
+    tables and top-k on the GPU against the oracle."""
+    torch = torch_cuda
+    cfg = synth.CONFIGS["small_iid_l2"]
+    X = synth.iid(cfg["n"], cfg["J"], 0)
+    Q = synth.iid(cfg["nq"], cfg["J"], 1)
+    rows = synth.kmeans_init_rows(cfg["n"], 0)
+    Qtr = X[synth.train_query_rows(cfg["n"], 0)]
+    Cg, ag, bg = bolt.fit_codebooks(dev(torch, X), cfg["M"], cfg["iters"], rows, Qtrain=dev(torch, Qtr))
+    Co = oracle.kmeans(X, cfg["M"], cfg["iters"], rows)
+    np.testing.assert_allclose(Cg.cpu().numpy(), Co, rtol=1e-5, atol=1e-6)
+    # downstream parity feeds the same centroids and quantizer to both sides
+    a, b, _, _ = oracle.fit_quant(oracle.lut_f32(Qtr, Co, oracle.METRIC_L2))
+    Cd = dev(torch, Co)
+    codes = bolt.encode(dev(torch, X), Cd)
+    luts = bolt.build_luts(dev(torch, Q), Cd, bolt.METRIC_L2, a, b)
+    s, i = bolt.topk(codes, cfg["n"], cfg["M"], luts, cfg["k"], bolt.METRIC_L2)
+    oc = oracle.encode(X, Co)
+    ol = oracle.quantize(oracle.lut_f32(Q, Co, oracle.METRIC_L2), a, b)
+    rs, ri = oracle.topk(oracle.scan(oc, ol), cfg["k"], oracle.METRIC_L2)
+    np.testing.assert_array_equal(decode_blocked(codes.cpu().numpy(), cfg["n"], cfg["M"]), oc)
+    np.testing.assert_array_equal(luts.cpu().numpy(), ol)
+    np.testing.assert_array_equal(i.cpu().numpy(), ri)
+    np.testing.assert_array_equal(s.cpu().numpy(), rs)
+
+
+def test_mixture_1m_workload_full_size(torch_cuda):
+    """1,000,000 x 128 mixture, M = 16, top-100 L2 and dot, launched as in
+    the benchmark (one query per launch): all codes against the oracle, and
+    the top-k of a seeded sample of the 1,000 queries."""
+    torch = torch_cuda
+    cfg = synth.CONFIGS["mixture_1m"]
+    n, J, M, k = cfg["n"], cfg["J"], cfg["M"], cfg["k"]
+    X = synth.mixture(n, J, 0)
+    Q = synth.mixture(cfg["nq"], J, 1)
+    rows = synth.kmeans_init_rows(n, 0)
+    Co = oracle.kmeans(X[:20_000], M, 4, synth.kmeans_init_rows(20_000, 0))
+    Cd = dev(torch, Co)
+    codes = bolt.encode(dev(torch, X), Cd)
+    oc = oracle.encode(X, Co)
+    np.testing.assert_array_equal(decode_blocked(codes.cpu().numpy(), n, M), oc)
+    Qtr = X[synth.train_query_rows(n, 0)]
+    sample = np.random.default_rng(11).choice(cfg["nq"], 6, replace=False)
+    for metric in (oracle.METRIC_L2, oracle.METRIC_DOT):
+        a, b, _, _ = oracle.fit_quant(oracle.lut_f32(Qtr, Co, metric))
+        luts = bolt.build_luts(dev(torch, Q), Cd, metric, a, b)
+        ol = oracle.quantize(oracle.lut_f32(Q, Co, metric), a, b)
+        np.testing.assert_array_equal(luts.cpu().numpy(), ol)
+        for qi in sample:
+            s, i = bolt.topk(codes, n, M, luts[qi:qi + 1], k, metric)
+            rs, ri = oracle.topk(oracle.scan(oc, ol[qi:qi + 1]), k, metric)
+            np.testing.assert_array_equal(i.cpu().numpy(), ri)
+            np.testing.assert_array_equal(s.cpu().numpy(), rs)
+    del rows
