@@ -43,6 +43,11 @@ __host__ __device__ inline int64_t num_blocks(int64_t n) { return (n + kBlockVec
 
 int device_sm_count();  // SMs of the current device (cached per device)
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (device, kernel)
+// and size: later launches (including ones under stream capture) make no
+// attribute call.
+int ensure_smem(const void *func, size_t bytes);
+
 // Shape checks shared by the entry points.
 int check_nm(int64_t n, int32_t M);
 int check_jm(int32_t J, int32_t M);

@@ -75,7 +75,8 @@ int launch_encode_fp32(const float *X, int64_t n, int32_t J, int32_t M, const fl
     if (nb == 0) return BOLT_OK;
     const size_t smem = (size_t)J * kK * sizeof(float);
     BOLT_REQUIRE(smem <= 200 * 1024, BOLT_EUNSUPPORTED, "J=%d too large for the fp32 encoder", J);
-    BOLT_CUDA(cudaFuncSetAttribute(encode_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int rc = ensure_smem((const void *)encode_fp32_kernel, smem);
+    if (rc) return rc;
     int64_t grid = nb;
     const int64_t cap = (int64_t)device_sm_count() * 8;
     if (cap > 0 && grid > cap) grid = cap;

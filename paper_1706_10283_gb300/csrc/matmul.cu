@@ -108,12 +108,8 @@ int bolt_approx_matmul(const float *A, int64_t rows, int32_t J, const uint8_t *c
     if (rc == BOLT_OK) {
         constexpr int QB = 8;
         const size_t smem = (size_t)QB * M * 16;
-        cudaError_t e = cudaFuncSetAttribute(bolt::approx_matmul_kernel<QB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) {
-            bolt::set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-            rc = BOLT_ECUDA;
-        } else {
+        rc = bolt::ensure_smem((const void *)bolt::approx_matmul_kernel<QB>, smem);
+        if (rc == BOLT_OK) {
             const int64_t nb = bolt::num_blocks(n);
             const int64_t row_tiles = (rows + QB - 1) / QB;
             int64_t gx = (nb + 7) / 8;

@@ -18,6 +18,18 @@
 
 namespace bolt {
 
+// Multipliers kept in constant memory so the compiler cannot fold them: the
+// adds and the left shift of the lookup then issue as IMAD on the FMA pipe,
+// leaving the integer ALU pipe (which runs prmt and lop3) to the lookups.
+__constant__ uint32_t kMulOne = 1u;
+__constant__ uint32_t kMulShl4 = 16u;
+
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
 struct WordSel {
     uint32_t s_lo;  // low 3 code bits of vectors 0..3 as prmt selectors (low 16 bits)
     uint32_t s_hi;  // same for vectors 4..7
@@ -30,7 +42,7 @@ __device__ __forceinline__ WordSel prep_word(uint32_t W) {
     const uint32_t s7 = W & 0x77777777u;
     r.s_lo = s7;
     r.s_hi = s7 >> 16;
-    const uint32_t Wsh = W << 4;
+    const uint32_t Wsh = imad(W, kMulShl4, 0u);  // W << 4
     // Sign-replicating selectors: output byte i copies the top bit of the byte
     // holding bit 3 of vector i's code (bit 3 of W's byte, shifted into bit 7
     // of Wsh's byte for even vectors).
@@ -53,10 +65,11 @@ struct Acc8 {
     __device__ __forceinline__ void add(const WordSel &w, uint4 t) {
         const uint32_t ra = lookup4(t.x, t.y, t.z, t.w, w.s_lo, w.m_lo);
         const uint32_t rb = lookup4(t.x, t.y, t.z, t.w, w.s_hi, w.m_hi);
-        full_lo += ra;
-        odd_lo += prmt(ra, 0u, 0x4341u);
-        full_hi += rb;
-        odd_hi += prmt(rb, 0u, 0x4341u);
+        const uint32_t one = kMulOne;
+        full_lo = imad(ra, one, full_lo);
+        odd_lo = imad(prmt(ra, 0u, 0x4341u), one, odd_lo);
+        full_hi = imad(rb, one, full_hi);
+        odd_hi = imad(prmt(rb, 0u, 0x4341u), one, odd_hi);
     }
     // Packed results: e = (S0 | S2 << 16), o = (S1 | S3 << 16) etc.
     __device__ __forceinline__ void finish(uint32_t &e_lo, uint32_t &o_lo, uint32_t &e_hi,

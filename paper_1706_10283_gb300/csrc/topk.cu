@@ -2,8 +2,9 @@
 // inner product for dot sums; Sec. 1.2 motivates both searches).
 //
 // Keys.  A candidate is the 64-bit key (s' << 32 | index) with s' = S for L2
-// and s' = 0xFFFF - S for dot, so "smaller key" is "better" for both metrics
-// and equal sums break ties toward the lower index.
+// and s' = 255*M - S for dot, so "smaller key" is "better" for both metrics
+// and equal sums break ties toward the lower index.  Bit 63 marks a candidate
+// already counted in the global histogram (masked out of every comparison).
 //
 // Work split.  Each query is handled by `grid` CTAs, one contiguous range of
 // 256-vector code blocks per CTA.  A CTA processes its blocks in rounds: in
@@ -12,17 +13,23 @@
 // blocks through a private ring of shared-memory stages filled by 1-D TMA
 // bulk copies (non-multicast) completing on an mbarrier.
 //
-// Candidates.  Lanes append sums below the CTA's threshold s_thr to a
-// shared buffer.  When the buffer runs full the CTA finds s* = the k-th
-// smallest s' (two 8-bit histogram passes), keeps every entry with s' <= s*
-// and sets s_thr = s*: later blocks only hold larger indices, so an equal
-// sum can no longer enter the top k.  The CTA then publishes s* to a
-// per-query global bound (some CTA holds k entries <= s*), which every CTA
-// uses to reject s' > s*.
+// Candidates.  Lanes append sums below the CTA's threshold to a shared
+// buffer.  When it runs full the CTA histograms the buffer by s' bin (4096
+// bins of width 2^hshift), keeps every entry up to the bin of its k-th
+// smallest and lowers its threshold: later blocks only hold larger indices,
+// so with unit bins an equal sum can no longer enter the top k.
 //
-// Merge.  Each CTA writes its exact top k; the last CTA to finish (atomic
-// ticket) loads all lists into shared memory, selects the exact k smallest
-// keys, sorts them and writes the result.
+// Global bound.  Every CTA adds each candidate it keeps, once, to a
+// per-query global histogram of s' bins.  Those are distinct vectors, so the
+// bin where the histogram's running count reaches k bounds the k-th smallest
+// sum of the whole query; every CTA reads it back at compactions and every
+// 32 rounds and rejects sums in later bins.
+//
+// Merge.  Each CTA appends its candidates up to the current global bound
+// (at most 2k, else its exact top k) to a per-query list; the last CTA to
+// finish (atomic ticket) finds the final bound bin from the histogram,
+// gathers the few candidates at or below it into shared memory, selects the
+// exact k smallest keys, sorts them and writes the result.
 #include "scan_core.cuh"
 #include "topk.cuh"
 
@@ -39,11 +46,16 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+constexpr uint64_t kFlag = 1ull << 63;  // "already counted in the global histogram"
+
+__device__ __forceinline__ uint64_t kv(uint64_t key) { return key & ~kFlag; }
+
 // ------------------------------------------------------------------ block-wide selection
+// Exact radix selection over keys (byte digits, warp-aggregated counts).
 template <int T>
 struct BlockSel {
     uint32_t *hist;  // 256 counters
-    uint32_t *res;   // [0] digit, [1] count below digit, [2..2+T/32) warp counts
+    uint32_t *res;   // [0] digit, [1] count below digit
 
     // Histogram of the byte at `shift` over keys whose bits above the byte
     // match `prefix` (bits above shift+8), warp-aggregated.
@@ -56,7 +68,7 @@ struct BlockSel {
             const int i = base + tid;
             uint32_t bin = 0xFFFFFFFFu;
             if (i < cnt) {
-                const uint64_t key = keys[i];
+                const uint64_t key = kv(keys[i]);
                 if ((key & hmask) == (prefix & hmask)) bin = (uint32_t)(key >> shift) & 255u;
             }
             const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin);
@@ -131,31 +143,6 @@ struct BlockSel {
         return prefix;
     }
 
-    // Stable in-place compaction keeping keys <= bound; returns the new count.
-    __device__ int keep_le(uint64_t *keys, int cnt, uint64_t bound) {
-        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-        uint32_t *wcnt = res + 2;
-        int out = 0;
-        for (int base = 0; base < cnt; base += T) {
-            const int i = base + tid;
-            const uint64_t key = i < cnt ? keys[i] : ~0ull;
-            const bool keep = i < cnt && key <= bound;
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
-            if (lane == 0) wcnt[warp] = __popc(bal);
-            __syncthreads();
-            int off = 0, tot = 0;
-            for (int w = 0; w < T / 32; ++w) {
-                const int c = wcnt[w];
-                off += w < warp ? c : 0;
-                tot += c;
-            }
-            if (keep) keys[out + off + __popc(bal & lanemask_lt())] = key;
-            out += tot;
-            __syncthreads();
-        }
-        return out;
-    }
-
     // Bitonic sort of keys[0..P), P a power of two.
     __device__ void sort_pow2(uint64_t *keys, int P) {
         for (int size = 2; size <= P; size <<= 1) {
@@ -177,16 +164,121 @@ struct BlockSel {
 };
 
 // ------------------------------------------------------------------ kernel
-template <int WARPS>
+constexpr uint32_t kThrAll = 0x10000u;  // insert iff s' < thr: everything passes
+constexpr int kRankSortMax = 1024;      // merge sorts by rank counting up to this many keys
+constexpr int kTmpKeys = kBins / 2;     // survivors that fit in the histogram area as keys
+
+// Block-wide histogram of the buffer over s' bins and k-th bin search.
+template <int T>
+struct BinSel {
+    uint32_t *hist;  // kBins counters
+    uint32_t *res;   // [0] bin, [1] count with bin <= res[0], [2..2+T/32) warp sums
+    int hshift;
+
+    __device__ void clear() {
+        for (int i = threadIdx.x; i < kBins; i += T) hist[i] = 0;
+        __syncthreads();
+    }
+    __device__ void count(const uint64_t *keys, int cnt) {
+        clear();
+        for (int i = threadIdx.x; i < cnt; i += T) atomicAdd(&hist[(uint32_t)(kv(keys[i]) >> 32) >> hshift], 1u);
+        __syncthreads();
+    }
+    // Copy the global histogram in: every load is issued before any store so
+    // the L2 round trips overlap.
+    __device__ void load_global(const uint32_t *g) {
+        constexpr int BPT = kBins / T;
+        uint32_t v[BPT];
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) v[i] = __ldcg(g + threadIdx.x + i * T);
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) hist[threadIdx.x + i * T] = v[i];
+        __syncthreads();
+    }
+    // Smallest bin b with (#entries in bins <= b) >= kk: res[0] = b, res[1] =
+    // that count.  res[0] = kBins and res[1] = total when total < kk.
+    __device__ void find(uint32_t kk) {
+        constexpr int BPT = kBins / T;
+        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+        uint32_t *wsum = res + 2;
+        uint32_t local = 0;
+#pragma unroll 8
+        for (int i = 0; i < BPT; ++i) local += hist[tid * BPT + i];
+        uint32_t incl = local;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+            if (lane >= off) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        if (tid == 0) {
+            res[0] = kBins;
+            res[1] = 0;
+        }
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < T / 32; ++w) {
+            const uint32_t c = wsum[w];
+            before += w < warp ? c : 0;
+            total += c;
+        }
+        const uint32_t excl = before + incl - local;
+        if (total < kk) {
+            if (tid == 0) res[1] = total;
+        } else if (excl < kk && kk <= excl + local) {
+            uint32_t c = excl;
+            for (int i = 0; i < BPT; ++i) {
+                c += hist[tid * BPT + i];
+                if (c >= kk) {
+                    res[0] = tid * BPT + i;
+                    res[1] = c;
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+    }
+};
+
+// Stable in-place compaction of keys[0..cnt) keeping pred(key); returns the
+// new count.  wcnt: T/32 scratch words.
+template <int T, typename P>
+__device__ int keep_if(uint64_t *keys, int cnt, uint32_t *wcnt, P pred) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int out = 0;
+    for (int base = 0; base < cnt; base += T) {
+        const int i = base + tid;
+        const uint64_t key = i < cnt ? keys[i] : 0ull;
+        const bool keep = i < cnt && pred(key);
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int w = 0; w < T / 32; ++w) {
+            const int c = wcnt[w];
+            off += w < warp ? c : 0;
+            tot += c;
+        }
+        if (keep) keys[out + off + __popc(bal & lanemask_lt())] = key;
+        out += tot;
+        __syncthreads();
+    }
+    return out;
+}
+
+// MT > 0 fixes the codebook count at compile time (fully unrolled lookups);
+// MT = 0 reads it from M.
+template <int WARPS, int MT>
 __global__ void __launch_bounds__(WARPS * 32, 1)
     topk_kernel(const uint32_t *__restrict__ codes, int64_t n, int32_t M, const uint8_t *__restrict__ luts,
-                int32_t k, int32_t metric, TopkWS ws, int stages, int cap, int64_t blocks_per_cta,
-                uint16_t *__restrict__ out_sums, int64_t *__restrict__ out_idx) {
+                int32_t k, int32_t metric, TopkWS ws, int stages, int cap, int hshift, int64_t blocks_per_cta,
+                int out_cap, uint16_t *__restrict__ out_sums, int64_t *__restrict__ out_idx) {
     constexpr int T = WARPS * 32;
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t q = blockIdx.y;
     const int G = gridDim.x, cta = blockIdx.x;
+    if (MT > 0) M = MT;
     const uint32_t stage_bytes = (uint32_t)M * kRowBytes;
 
     uint8_t *p = smem;
@@ -199,28 +291,36 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     uint64_t *bars = reinterpret_cast<uint64_t *>(p);
     p += (size_t)WARPS * kMaxStages * 8;
     uint32_t *hist = reinterpret_cast<uint32_t *>(p);
-    p += 256 * 4;
-    uint32_t *misc = reinterpret_cast<uint32_t *>(p);  // [0] cnt [1] thr [2] flags [3] last [4..] sel scratch
-    BlockSel<T> sel{hist, misc + 4};
+    p += kBins * 4;
+    uint32_t *misc = reinterpret_cast<uint32_t *>(p);
+    // misc: [0] buffer count [1] insert threshold [2] failure flag [3] last CTA
+    //       [4] scratch [8..26) BinSel results [32..48) keep_if counts [64..66) BlockSel
+    BinSel<T> bins{hist, misc + 8, hshift};
+    BlockSel<T> sel{hist, misc + 64};
+    uint32_t *wcnt = misc + 32;
     volatile uint32_t *vmisc = misc;
+    uint32_t *ghist = ws.ghist + q * kBins;
 
     const uint4 *lut_g = reinterpret_cast<const uint4 *>(luts + q * M * kK);
     for (int i = tid; i < M; i += T) lut[i] = lut_g[i];
     if (tid == 0) {
         misc[0] = 0;
-        misc[1] = 0x10000u;  // insert iff s' < thr: everything passes
+        misc[1] = kThrAll;
         misc[2] = 0;
         misc[3] = 0;
+        misc[6] = 0;  // cooperative-phase requests
+        misc[7] = 0;  // warps out of blocks
     }
     if (tid < WARPS * stages) mbar_init(&bars[tid], 1);
     fence_mbar_init();
     __syncthreads();
 
-    const int64_t nb = num_blocks(n);
-    const int64_t b_lo = (int64_t)cta * blocks_per_cta;
-    const int64_t b_hi = min(nb, b_lo + blocks_per_cta);
-    const int64_t nbc = b_hi > b_lo ? b_hi - b_lo : 0;
-    const int64_t rounds = (nbc + WARPS - 1) / WARPS;
+    // Block indices fit in 32 bits (n < 2^31 vectors).
+    const uint32_t nb = (uint32_t)num_blocks(n);
+    const uint32_t b_lo = (uint32_t)min((int64_t)nb, (int64_t)cta * blocks_per_cta);
+    const uint32_t b_hi = (uint32_t)min((int64_t)nb, (int64_t)b_lo + blocks_per_cta);
+    const uint32_t last_block = nb - 1;  // the only block that can hold vectors past n
+    const uint32_t blk_words = (uint32_t)M * kRowWords;
     uint64_t *mybars = bars + warp * stages;
     uint8_t *mystage = stage_base + (size_t)warp * stages * stage_bytes;
 
@@ -229,100 +329,274 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     uint32_t phase = 0;    // parity of the next completion of each stage (lane 0)
     if (lane == 0) {
         for (int s = 0; s < stages; ++s) {
-            const int64_t b = b_lo + (int64_t)s * WARPS + warp;
+            const uint32_t b = b_lo + (uint32_t)s * WARPS + warp;
             if (b < b_hi) {
                 mbar_arrive_expect_tx(&mybars[s], stage_bytes);
-                bulk_g2s(mystage + (size_t)s * stage_bytes, codes + b * M * kRowWords, stage_bytes, &mybars[s]);
+                bulk_g2s(mystage + (size_t)s * stage_bytes, codes + (size_t)b * blk_words, stage_bytes, &mybars[s]);
                 pending |= 1u << s;
             }
         }
     }
 
-    bool failed = false;
-    const uint32_t gate = (uint32_t)(cap - WARPS * kBlockVecs);  // compact above this count
-    for (int64_t r = 0; r < rounds; ++r) {
-        const int64_t b = b_lo + r * WARPS + warp;
-        const int st = (int)(r % stages);
-        const uint32_t par = (uint32_t)((r / stages) & 1);
-        if (b < b_hi && !failed) {
-            const bool ok = mbar_wait_bounded(&mybars[st], par, kWaitLimit);
-            if (!__all_sync(0xFFFFFFFFu, ok)) {
-                failed = true;
-            } else {
-                if (lane == 0) {
-                    pending &= ~(1u << st);
-                    phase ^= 1u << st;
-                }
-                const uint32_t *words = reinterpret_cast<const uint32_t *>(mystage + (size_t)st * stage_bytes);
-                Acc8 acc;
-                acc.zero();
-#pragma unroll 4
-                for (int m = 0; m < M; ++m) acc.add(prep_word(words[m * kRowWords + lane]), lut[m]);
-                __syncwarp();
-                if (lane == 0) {
-                    const int64_t b2 = b + (int64_t)stages * WARPS;
-                    if (b2 < b_hi) {
-                        mbar_arrive_expect_tx(&mybars[st], stage_bytes);
-                        bulk_g2s(mystage + (size_t)st * stage_bytes, codes + b2 * M * kRowWords, stage_bytes,
-                                 &mybars[st]);
-                        pending |= 1u << st;
-                    }
-                }
-                uint32_t e_lo, o_lo, e_hi, o_hi;
-                acc.finish(e_lo, o_lo, e_hi, o_hi);
-                if (metric == BOLT_METRIC_DOT) {  // s' = 0xFFFF - S in each 16-bit lane
-                    e_lo = ~e_lo;
-                    o_lo = ~o_lo;
-                    e_hi = ~e_hi;
-                    o_hi = ~o_hi;
-                }
-                const uint32_t thr = vmisc[1];
-                const uint32_t mn2 = __vminu2(__vminu2(e_lo, o_lo), __vminu2(e_hi, o_hi));
-                const uint32_t mn = min(mn2 & 0xFFFFu, mn2 >> 16);
-                const int64_t v0 = b * kBlockVecs + 8 * lane;
-                const bool maybe = mn < thr && v0 < n;
-                if (__any_sync(0xFFFFFFFFu, maybe)) {
-                    const uint4 pk = pack_sums(e_lo, o_lo, e_hi, o_hi);
-                    const uint32_t w4[4] = {pk.x, pk.y, pk.z, pk.w};
+    // Global bound.  prefetch(): issue the loads of the global histogram into
+    // registers.  finish(): hist := that snapshot plus this CTA's entries not
+    // yet counted, which are also added to the global histogram and flagged;
+    // then lower the threshold to the bin holding the k-th smallest count.
+    constexpr int GPT = kBins / T;
+    uint32_t gv[GPT];
+    auto prefetch = [&]() {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const uint32_t sp = (w4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
-                        const bool pred = sp < thr && v0 + i < n;
-                        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, pred);
-                        if (bal) {
-                            const int leader = __ffs(bal) - 1;
-                            uint32_t base = 0;
-                            if (lane == leader) base = atomicAdd(&misc[0], (uint32_t)__popc(bal));
-                            base = __shfl_sync(0xFFFFFFFFu, base, leader);
-                            if (pred)
-                                keys[base + __popc(bal & lanemask_lt())] =
-                                    ((uint64_t)sp << 32) | (uint64_t)(uint32_t)(v0 + i);
-                        }
-                    }
-                }
+        for (int i = 0; i < GPT; ++i) gv[i] = __ldcg(ghist + tid + i * T);
+    };
+    auto finish = [&](int cnt) -> uint32_t {
+#pragma unroll
+        for (int i = 0; i < GPT; ++i) hist[tid + i * T] = gv[i];
+        __syncthreads();
+        for (int i = tid; i < cnt; i += T) {
+            const uint64_t key = keys[i];
+            if (!(key & kFlag)) {
+                const uint32_t bin = (uint32_t)(key >> 32) >> hshift;
+                atomicAdd(&hist[bin], 1u);
+                atomicAdd(&ghist[bin], 1u);
+                keys[i] = key | kFlag;
             }
         }
         __syncthreads();
-        if (vmisc[0] > gate) {
-            // Buffer full: keep every entry with s' <= s* (k-th smallest s').
-            const int cnt = (int)vmisc[0];
-            uint32_t n_less, n_eq;
-            const uint32_t s_star = sel.kth_sum(keys, cnt, (uint32_t)k, n_less, n_eq);
-            uint64_t bound = ((uint64_t)s_star << 32) | 0xFFFFFFFFull;
-            if (n_less + n_eq > gate) bound = sel.kth_key(keys, cnt, (uint32_t)k);  // pathological ties
-            const int kept = sel.keep_le(keys, cnt, bound);
+        bins.find((uint32_t)k);
+        const uint32_t bg = bins.res[0];
+        if (tid == 0 && bg < (uint32_t)kBins) {
+            const uint32_t gthr = (bg + 1u) << hshift;
+            if (gthr < vmisc[1]) vmisc[1] = gthr;
+        }
+        __syncthreads();
+        return bg;
+    };
+
+    bool failed = false;
+    const uint32_t smax = 255u * (uint32_t)M;  // largest possible sum
+    const uint32_t smax2 = smax | (smax << 16);
+    const bool swar = smax <= 0x7FFFu;  // sums fit in 15 bits (M <= 128)
+    const uint32_t gate = (uint32_t)(cap - WARPS * kBlockVecs);  // compact above this count
+    // before the first compaction: compact as soon as a few blocks are in
+    const uint32_t early = min(gate, max((uint32_t)(2 * k), (uint32_t)(WARPS * kBlockVecs)));
+    const uint32_t one = kMulOne;
+    bool compacted = false;  // same value in every thread (set in cooperative())
+
+    // Cooperative phases.  Warps run independently; a warp that needs the
+    // whole CTA sets a request bit in misc[6] (1: compact the buffer, 2:
+    // refresh the global bound) and every warp joins at its next check (the
+    // request is only cleared inside the phase, between two barriers, so each
+    // warp joins each phase exactly once).
+    auto cooperative = [&]() -> uint32_t {
+        __syncthreads();
+        const uint32_t f = vmisc[6];
+        const int cnt = (int)vmisc[0];
+        if (f & 1u) {
+            // Keep every entry up to the bin of the k-th smallest s'.
+            prefetch();  // global histogram loads overlap the local selection
+            bins.count(keys, cnt);
+            bins.find((uint32_t)k);
+            const uint32_t bstar = bins.res[0], c_le = bins.res[1];
+            int kept;
+            uint32_t own;
+            if (cnt <= k) {
+                kept = cnt;
+                own = vmisc[1];
+            } else if (c_le <= (uint32_t)kTmpKeys) {
+                // Few survivors: append them to the (now free) histogram area,
+                // then copy them back to the front of the buffer.
+                uint64_t *tmp = reinterpret_cast<uint64_t *>(hist);
+                if (tid == 0) misc[5] = 0;
+                __syncthreads();
+                for (int i0 = 0; i0 < cnt; i0 += T) {
+                    const int i = i0 + tid;
+                    const uint64_t key = i < cnt ? keys[i] : 0ull;
+                    const bool keep = i < cnt && ((uint32_t)(kv(key) >> 32) >> hshift) <= bstar;
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+                    if (bal) {
+                        const int leader = __ffs(bal) - 1;
+                        uint32_t base = 0;
+                        if (lane == leader) base = atomicAdd(&misc[5], (uint32_t)__popc(bal));
+                        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+                        if (keep) tmp[base + __popc(bal & lanemask_lt())] = key;
+                    }
+                }
+                __syncthreads();
+                kept = (int)vmisc[5];
+                for (int i = tid; i < kept; i += T) keys[i] = tmp[i];
+                __syncthreads();
+                own = hshift == 0 ? bstar : (bstar + 1u) << hshift;
+            } else if (c_le <= gate) {
+                kept = keep_if<T>(keys, cnt, wcnt,
+                                  [&](uint64_t key) { return ((uint32_t)(kv(key) >> 32) >> hshift) <= bstar; });
+                own = hshift == 0 ? bstar : (bstar + 1u) << hshift;
+            } else {  // one bin holds too many entries: exact k-th key
+                const uint64_t kth = sel.kth_key(keys, cnt, (uint32_t)k);
+                kept = keep_if<T>(keys, cnt, wcnt, [&](uint64_t key) { return kv(key) <= kth; });
+                own = (uint32_t)(kth >> 32);
+            }
             if (tid == 0) {
                 misc[0] = (uint32_t)kept;
-                misc[1] = min(vmisc[1], s_star);
-                atomicMax(&ws.ginv[q], ~s_star);  // this CTA holds k entries with s' <= s*
+                if (own < vmisc[1]) vmisc[1] = own;
             }
             __syncthreads();
+            finish(kept);
+            compacted = true;
+        } else {
+            prefetch();
+            finish(cnt);
         }
-        if (tid == 0 && (r & 7) == 7) {
-            // Fold in the global bound: entries with s' > g cannot be in the top k.
-            const uint32_t g = ~*reinterpret_cast<volatile uint32_t *>(&ws.ginv[q]);
-            const uint32_t gthr = g >= 0xFFFFu ? 0x10000u : g + 1u;
-            if (gthr < vmisc[1]) vmisc[1] = gthr;
+        if (tid == 0) misc[6] = 0;
+        __syncthreads();
+        return f;
+    };
+    auto requests = [&]() -> uint32_t {
+        uint32_t f = lane == 0 ? vmisc[6] : 0u;
+        return __shfl_sync(0xFFFFFFFFu, f, 0);
+    };
+
+    uint32_t st = 0, par = 0;  // stage and parity of this warp's current block
+    uint32_t j = 0;            // blocks done by this warp
+    uint32_t refresh_j = 0xFFFFFFFFu;
+    for (uint32_t b = b_lo + warp;; b += WARPS, ++j) {
+        if (requests()) {
+            const uint32_t f = cooperative();
+            if (f & 1u) refresh_j = j + 2;  // refresh again once the other CTAs have published
+        }
+        if (b >= b_hi || failed) break;
+        if (!__all_sync(0xFFFFFFFFu, mbar_try_wait(&mybars[st], par))) {
+            const bool ok = mbar_wait_bounded(&mybars[st], par, kWaitLimit);
+            if (!__all_sync(0xFFFFFFFFu, ok)) {
+                failed = true;
+                continue;
+            }
+        }
+        const uint32_t *words = reinterpret_cast<const uint32_t *>(mystage + (size_t)st * stage_bytes);
+        Acc8 acc;
+        acc.zero();
+        if (MT > 0) {
+#pragma unroll
+            for (int m = 0; m < MT; ++m) acc.add(prep_word(words[m * kRowWords + lane]), lut[m]);
+        } else {
+#pragma unroll 4
+            for (int m = 0; m < M; ++m) acc.add(prep_word(words[m * kRowWords + lane]), lut[m]);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            pending &= ~(1u << st);
+            phase ^= 1u << st;
+            const uint32_t b2 = b + (uint32_t)stages * WARPS;
+            if (b2 < b_hi) {
+                mbar_arrive_expect_tx(&mybars[st], stage_bytes);
+                bulk_g2s(mystage + (size_t)st * stage_bytes, codes + (size_t)b2 * blk_words, stage_bytes,
+                         &mybars[st]);
+                pending |= 1u << st;
+            }
+        }
+        if (++st == (uint32_t)stages) {
+            st = 0;
+            par ^= 1u;
+        }
+        uint32_t e_lo, o_lo, e_hi, o_hi;
+        acc.finish(e_lo, o_lo, e_hi, o_hi);
+        if (metric == BOLT_METRIC_DOT) {  // s' = 255*M - S in each 16-bit lane (no borrow)
+            e_lo = smax2 - e_lo;
+            o_lo = smax2 - o_lo;
+            e_hi = smax2 - e_hi;
+            o_hi = smax2 - o_hi;
+        }
+        const uint32_t v0 = b * kBlockVecs + 8u * lane;
+        const bool tail = b == last_block;
+        uint32_t thr = vmisc[1];
+        bool maybe = true;
+        if (swar && thr <= 0x7FFFu) {
+            // s' < 2^15: the top bit of (s' + 2^15 - thr) in each lane is clear
+            // exactly when s' < thr, with no borrow between lanes.
+            const uint32_t nt2 = 0u - (thr | (thr << 16));
+            const uint32_t d = imad(e_lo | 0x80008000u, one, nt2) & imad(o_lo | 0x80008000u, one, nt2) &
+                               imad(e_hi | 0x80008000u, one, nt2) & imad(o_hi | 0x80008000u, one, nt2);
+            maybe = (~d & 0x80008000u) != 0u;
+        }
+        if (tail) maybe = maybe && v0 < (uint32_t)n;
+        if (__any_sync(0xFFFFFFFFu, maybe)) {
+            const uint4 pk = pack_sums(e_lo, o_lo, e_hi, o_hi);
+            const uint32_t w4[4] = {pk.x, pk.y, pk.z, pk.w};
+            for (int attempt = 0;; ++attempt) {
+                // One warp prefix sum places every lane's candidates; the slots
+                // are reserved with a compare-and-swap that never passes cap.
+                uint32_t cm = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const uint32_t sp = (w4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                    if (sp < thr && (!tail || v0 + i < (uint32_t)n)) cm |= 1u << i;
+                }
+                const uint32_t c = __popc(cm);
+                uint32_t incl = c;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+                    if (lane >= off) incl += t;
+                }
+                uint32_t base = 0, ok = 1;
+                if (lane == 31 && incl) {
+                    ok = 0;
+                    for (int spin = 0; spin < (1 << 20); ++spin) {
+                        const uint32_t old = vmisc[0];
+                        if (old + incl > (uint32_t)cap) break;
+                        if (atomicCAS(&misc[0], old, old + incl) == old) {
+                            base = old;
+                            ok = 1;
+                            break;
+                        }
+                    }
+                }
+                ok = __shfl_sync(0xFFFFFFFFu, ok, 31);
+                if (ok) {
+                    base = __shfl_sync(0xFFFFFFFFu, base, 31);
+                    uint32_t pos = base + incl - c;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        if (cm & (1u << i)) {
+                            const uint32_t sp = (w4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                            keys[pos++] = ((uint64_t)sp << 32) | (uint64_t)(v0 + i);
+                        }
+                    }
+                    break;
+                }
+                // Buffer full: compact with the whole CTA, then retry with the
+                // tighter threshold.
+                if (lane == 0) atomicOr(&misc[6], 1u);
+                const uint32_t f = cooperative();
+                if (f & 1u) refresh_j = j + 2;
+                thr = vmisc[1];
+            }
+            if (lane == 0 && vmisc[0] > (compacted ? gate : early)) atomicOr(&misc[6], 1u);
+        }
+        if (warp == 0 && lane == 0 && (j == refresh_j || (j & 31u) == 31u)) atomicOr(&misc[6], 2u);
+    }
+    // This warp is out of blocks: keep joining cooperative phases until every
+    // warp is done (each of them reaches this point in bounded time).
+    if (lane == 0) atomicAdd(&misc[7], 1u);
+    {
+        const uint64_t t0 = globaltimer_ns();
+        while (true) {
+            uint32_t f = 0, d = 0;
+            if (lane == 0) {
+                f = vmisc[6];
+                d = vmisc[7];
+            }
+            f = __shfl_sync(0xFFFFFFFFu, f, 0);
+            d = __shfl_sync(0xFFFFFFFFu, d, 0);
+            if (f) {
+                cooperative();
+                continue;
+            }
+            if (d == (uint32_t)WARPS) break;
+            __nanosleep(64);
+            if (globaltimer_ns() - t0 > 4 * kWaitLimit) {
+                failed = true;
+                break;
+            }
         }
     }
     __syncthreads();
@@ -336,18 +610,22 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     if (failed) atomicOr(&misc[2], 1u);
     __syncthreads();
 
-    // Exact top k of this CTA.
+    // Candidates of this CTA up to the global bound (at most 2k of them).
     int cnt = (int)vmisc[0];
-    if (cnt > k) {
+    prefetch();
+    const uint32_t bg = finish(cnt);
+    cnt = keep_if<T>(keys, cnt, wcnt,
+                     [&](uint64_t key) { return ((uint32_t)(kv(key) >> 32) >> hshift) <= bg; });
+    if (cnt > out_cap) {
         const uint64_t kth = sel.kth_key(keys, cnt, (uint32_t)k);
-        cnt = sel.keep_le(keys, cnt, kth);
+        cnt = keep_if<T>(keys, cnt, wcnt, [&](uint64_t key) { return kv(key) <= kth; });
     }
-    uint64_t *cand = ws.cand + ((int64_t)q * G + cta) * k;
-    for (int i = tid; i < cnt; i += T) cand[i] = keys[i];
-    if (tid == 0) {
-        ws.cnt[q * G + cta] = (uint32_t)cnt;
-        if (misc[2]) atomicOr(&ws.status[q], 1u);
-    }
+    if (tid == 0) misc[4] = atomicAdd(&ws.fill[q], (uint32_t)cnt);
+    __syncthreads();
+    uint64_t *list = ws.cand + q * (int64_t)(out_cap * G);
+    const uint32_t base = vmisc[4];
+    for (int i = tid; i < cnt; i += T) list[base + i] = kv(keys[i]);
+    if (tid == 0 && misc[2]) atomicOr(&ws.status[q], 1u);
     __threadfence();
     __syncthreads();
     if (tid == 0) misc[3] = (atomicAdd(&ws.ticket[q], 1u) == (uint32_t)(G - 1)) ? 1u : 0u;
@@ -355,43 +633,55 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     if (vmisc[3] == 0) return;
     __threadfence();
 
-    // Last CTA: merge the G lists in shared memory.
+    // Last CTA: final bound from the complete histogram, gather, select, sort.
+    const uint32_t total = __ldcg(&ws.fill[q]);
+    bins.load_global(ghist);
+    bins.find((uint32_t)k);
+    const uint32_t bfin = bins.res[0];
     uint64_t *mk = reinterpret_cast<uint64_t *>(smem);
-    int total = 0;
-    for (int c = 0; c < G; ++c) {
-        const int cc = (int)__ldcg(&ws.cnt[q * G + c]);
-        const uint64_t *src = ws.cand + ((int64_t)q * G + c) * k;
-        for (int i = tid; i < cc; i += T) mk[total + i] = __ldcg(src + i);
-        total += cc;
-    }
+    if (tid == 0) misc[4] = 0;
     __syncthreads();
-    int kout = total < k ? total : k;
-    if (total > k) {
-        const uint64_t kth = sel.kth_key(mk, total, (uint32_t)k);
-        kout = sel.keep_le(mk, total, kth);
-    }
-    int P = 1;
-    while (P < kout) P <<= 1;
-    for (int i = kout + tid; i < P; i += T) mk[i] = ~0ull;
-    __syncthreads();
-    sel.sort_pow2(mk, P);
-    const bool bad = __ldcg(&ws.status[q]) != 0u;
-    for (int r = tid; r < k; r += T) {
-        uint16_t s = 0;
-        int64_t idx = -1;
-        if (r < kout) {
-            const uint64_t key = mk[r];
-            const uint32_t sp = (uint32_t)(key >> 32);
-            s = (uint16_t)(metric == BOLT_METRIC_DOT ? 0xFFFFu - sp : sp);
-            idx = (int64_t)(uint32_t)key;
+    for (uint32_t e0 = 0; e0 < total; e0 += 4 * T) {
+        uint64_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t e = e0 + u * T + tid;
+            v[u] = e < total ? __ldcg(list + e) : ~0ull;
         }
-        if (bad) idx = -2;
-        out_sums[q * k + r] = s;
-        out_idx[q * k + r] = idx;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (v[u] != ~0ull && ((uint32_t)(v[u] >> 32) >> hshift) <= bfin) mk[atomicAdd(&misc[4], 1u)] = v[u];
     }
-    if (tid == 0) {
-        ws.ticket[q] = 0;
-        ws.ginv[q] = 0;
+    __syncthreads();
+    int g = (int)vmisc[4];
+    const bool bad = __ldcg(&ws.status[q]) != 0u;
+    auto emit = [&](int r, uint64_t key) {
+        const uint32_t sp = (uint32_t)(key >> 32);
+        out_sums[q * k + r] = (uint16_t)(metric == BOLT_METRIC_DOT ? 255u * (uint32_t)M - sp : sp);
+        out_idx[q * k + r] = bad ? -2 : (int64_t)(uint32_t)key;
+    };
+    const int kout = g < k ? g : k;
+    if (g <= kRankSortMax) {
+        // Keys are unique: each key's rank is the number of smaller keys.
+        for (int e = tid; e < g; e += T) {
+            const uint64_t key = mk[e];
+            int rank = 0;
+            for (int j = 0; j < g; ++j) rank += mk[j] < key ? 1 : 0;
+            if (rank < k) emit(rank, key);
+        }
+    } else {
+        const uint64_t kth = sel.kth_key(mk, g, (uint32_t)k);
+        g = keep_if<T>(mk, g, wcnt, [&](uint64_t key) { return key <= kth; });
+        int P = 1;
+        while (P < kout) P <<= 1;
+        for (int i = kout + tid; i < P; i += T) mk[i] = ~0ull;
+        __syncthreads();
+        sel.sort_pow2(mk, P);
+        for (int r = tid; r < kout; r += T) emit(r, mk[r]);
+    }
+    for (int r = kout + tid; r < k; r += T) {
+        out_sums[q * k + r] = 0;
+        out_idx[q * k + r] = bad ? -2 : -1;
     }
 }
 
@@ -409,6 +699,8 @@ int plan_topk(int64_t n, int32_t M, int32_t k, TopkPlan *plan) {
     }
     BOLT_REQUIRE(stages >= 2, BOLT_EUNSUPPORTED, "M=%d too large for the top-k kernel", M);
     const int cap = (k + 15) / 16 * 16 + 2 * warps * kBlockVecs;  // multiple of 16: keeps later regions aligned
+    int hshift = 0;
+    while (((255 * M) >> hshift) >= kBins) ++hshift;
     const int64_t nb = num_blocks(n);
     const size_t region = (size_t)warps * stages * stage_bytes + (size_t)cap * 8;
     const int64_t merge_keys = (int64_t)(region / 8);
@@ -416,48 +708,55 @@ int plan_topk(int64_t n, int32_t M, int32_t k, TopkPlan *plan) {
     if (g <= 0) g = 1;
     const int64_t by_work = (nb + warps - 1) / warps;  // at least one full round per CTA
     if (g > by_work) g = by_work;
-    if (g > merge_keys / k) g = merge_keys / k;
+    if (g > merge_keys / k) g = merge_keys / k;  // the merge holds every CTA's list
     if (g < 1) g = 1;
+    int64_t out_cap = merge_keys / g;  // candidates one CTA may hand to the merge (>= k)
+    if (out_cap > 2 * k) out_cap = 2 * k;
     plan->warps = warps;
     plan->stages = stages;
     plan->grid = (int)g;
     plan->cap = cap;
+    plan->hshift = hshift;
+    plan->out_cap = (int)out_cap;
+    plan->list_cap = (int)(g * out_cap);
     plan->blocks_per_cta = nb > 0 ? (nb + g - 1) / g : 0;
-    plan->smem_bytes = region + align_up((size_t)M * 16, 16) + (size_t)warps * kMaxStages * 8 + 256 * 4 + 64 * 4;
+    plan->smem_bytes = region + align_up((size_t)M * 16, 16) + (size_t)warps * kMaxStages * 8 + kBins * 4 + 128 * 4;
     return BOLT_OK;
 }
 
-size_t topk_header_bytes(int64_t nq) { return align_up((size_t)nq * 12, 256); }
+size_t topk_header_bytes(int64_t nq) { return align_up((size_t)nq * 12, 256) + (size_t)nq * kBins * 4; }
 
 int64_t topk_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k) {
-    return (int64_t)(topk_header_bytes(nq) + align_up((size_t)nq * plan.grid * 4, 256) +
-                     (size_t)nq * plan.grid * k * 8);
+    (void)k;
+    return (int64_t)(topk_header_bytes(nq) + (size_t)nq * plan.list_cap * 8);
 }
 
 TopkWS carve_topk_ws(void *ws, const TopkPlan &plan, int64_t nq, int32_t k) {
     uint8_t *p = static_cast<uint8_t *>(ws);
     TopkWS w;
-    w.ginv = reinterpret_cast<uint32_t *>(p);
-    w.ticket = w.ginv + nq;
+    w.fill = reinterpret_cast<uint32_t *>(p);
+    w.ticket = w.fill + nq;
     w.status = w.ticket + nq;
-    p += topk_header_bytes(nq);
-    w.cnt = reinterpret_cast<uint32_t *>(p);
-    p += align_up((size_t)nq * plan.grid * 4, 256);
+    p += align_up((size_t)nq * 12, 256);
+    w.ghist = reinterpret_cast<uint32_t *>(p);
+    p += (size_t)nq * kBins * 4;
     w.cand = reinterpret_cast<uint64_t *>(p);
+    (void)plan;
     (void)k;
     return w;
 }
 
-template <int WARPS>
+template <int WARPS, int MT>
 static int launch_w(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, int32_t k,
                     int32_t metric, uint16_t *out_sums, int64_t *out_idx, const TopkWS &w, const TopkPlan &plan,
                     cudaStream_t stream) {
-    auto kern = topk_kernel<WARPS>;
-    BOLT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem_bytes));
+    auto kern = topk_kernel<WARPS, MT>;
+    int rc = ensure_smem((const void *)kern, plan.smem_bytes);
+    if (rc) return rc;
     dim3 grid(plan.grid, (unsigned)nq);
     kern<<<grid, WARPS * 32, plan.smem_bytes, stream>>>(reinterpret_cast<const uint32_t *>(codes), n, M, luts, k,
-                                                         metric, w, plan.stages, plan.cap, plan.blocks_per_cta,
-                                                         out_sums, out_idx);
+                                                         metric, w, plan.stages, plan.cap, plan.hshift,
+                                                         plan.blocks_per_cta, plan.out_cap, out_sums, out_idx);
     return check_launch("topk_kernel");
 }
 
@@ -467,12 +766,17 @@ int launch_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts,
     BOLT_REQUIRE(nq <= 65535, BOLT_EUNSUPPORTED, "nq=%lld > 65535 per call", (long long)nq);
     BOLT_CUDA(cudaMemsetAsync(workspace, 0, topk_header_bytes(nq), stream));
     const TopkWS w = carve_topk_ws(workspace, plan, nq, k);
-    switch (plan.warps) {
-        case 16: return launch_w<16>(codes, n, M, luts, nq, k, metric, out_sums, out_idx, w, plan, stream);
-        case 8: return launch_w<8>(codes, n, M, luts, nq, k, metric, out_sums, out_idx, w, plan, stream);
-        case 4: return launch_w<4>(codes, n, M, luts, nq, k, metric, out_sums, out_idx, w, plan, stream);
-        default: return launch_w<2>(codes, n, M, luts, nq, k, metric, out_sums, out_idx, w, plan, stream);
+#define BOLT_TOPK_ARGS codes, n, M, luts, nq, k, metric, out_sums, out_idx, w, plan, stream
+    if (plan.warps == 16) {
+        if (M == 8) return launch_w<16, 8>(BOLT_TOPK_ARGS);
+        if (M == 16) return launch_w<16, 16>(BOLT_TOPK_ARGS);
+        if (M == 32) return launch_w<16, 32>(BOLT_TOPK_ARGS);
+        return launch_w<16, 0>(BOLT_TOPK_ARGS);
     }
+    if (plan.warps == 8) return launch_w<8, 0>(BOLT_TOPK_ARGS);
+    if (plan.warps == 4) return launch_w<4, 0>(BOLT_TOPK_ARGS);
+    return launch_w<2, 0>(BOLT_TOPK_ARGS);
+#undef BOLT_TOPK_ARGS
 }
 
 }  // namespace bolt

@@ -5,28 +5,33 @@
 
 namespace bolt {
 
+constexpr int kBins = 4096;  // histogram bins over candidate sums
+
 struct TopkPlan {
     int warps;            // warps per CTA (16, 8, 4 or 2, by stage size)
     int stages;           // TMA stages per warp
     int grid;             // CTAs per query
     int cap;              // candidate-buffer entries per CTA
+    int hshift;           // histogram bin width 2^hshift
+    int out_cap;          // candidates one CTA may append (k <= out_cap <= 2k)
+    int list_cap;         // per-query candidate list capacity (grid * out_cap)
     int64_t blocks_per_cta;
     size_t smem_bytes;
 };
 
 // Per-query device state in the workspace.
 struct TopkWS {
-    uint32_t *ginv;    // [nq] bitwise NOT of the best published sum threshold (0 = none)
+    uint32_t *fill;    // [nq] entries appended to the candidate list
     uint32_t *ticket;  // [nq] CTAs finished
     uint32_t *status;  // [nq] bit 0: a bounded wait gave up
-    uint32_t *cnt;     // [nq][grid] candidates written by each CTA
-    uint64_t *cand;    // [nq][grid][k] candidate keys (sum' << 32 | index)
+    uint32_t *ghist;   // [nq][kBins] counted candidates per sum bin
+    uint64_t *cand;    // [nq][list_cap] candidate keys (sum' << 32 | index)
 };
 
 int plan_topk(int64_t n, int32_t M, int32_t k, TopkPlan *plan);
 int64_t topk_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k);
 TopkWS carve_topk_ws(void *ws, const TopkPlan &plan, int64_t nq, int32_t k);
-size_t topk_header_bytes(int64_t nq);
+size_t topk_header_bytes(int64_t nq);  // fill/ticket/status + histograms (zeroed per call)
 
 int launch_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, int32_t k,
                 int32_t metric, uint16_t *out_sums, int64_t *out_idx, void *workspace, const TopkPlan &plan,

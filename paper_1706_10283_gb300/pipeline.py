@@ -1,0 +1,123 @@
+"""One pass of the Bolt hot path as a reusable, graph-captured step.
+
+``SearchStep`` owns device buffers for a database of n vectors and nq queries
+and runs, in order (all in libbolt.so kernels):
+  1. encode the database (Sec. 3.1 h, K = 16),
+  2. build the uint8 query tables for each metric (Sec. 3.1 g, Sec. 3.2 beta),
+  3. scan + exact top-k, one query per launch (the plain GPU form),
+  4. dequantize the k best sums to distances / inner products (Sec. 3.2).
+The launch sequence is captured once into a CUDA graph and replayed, so the
+per-launch host overhead of the thousands of small launches is paid once.
+``run_from_host`` adds the host->device copy of the step's inputs from pinned
+memory and the device->host copy of its results.
+"""
+import torch
+
+from . import bolt
+
+
+class SearchStep:
+    def __init__(self, n, J, M, nq, k, centroids, quant, metrics=(bolt.METRIC_L2, bolt.METRIC_DOT),
+                 precision=bolt.PREC_FP32, device="cuda"):
+        self.n, self.J, self.M, self.nq, self.k = n, J, M, nq, k
+        self.metrics = tuple(metrics)
+        self.quant = dict(quant)  # metric -> (a, b)
+        self.precision = precision
+        dev = torch.device(device)
+        self.C = centroids
+        self.X = torch.empty((n, J), dtype=torch.float32, device=dev)
+        self.Q = torch.empty((nq, J), dtype=torch.float32, device=dev)
+        self.codes = torch.empty(bolt.codes_bytes(n, M), dtype=torch.uint8, device=dev)
+        self.luts = {m: torch.empty((nq, M, 16), dtype=torch.uint8, device=dev) for m in self.metrics}
+        self.sums = {m: torch.empty((nq, k), dtype=torch.uint16, device=dev) for m in self.metrics}
+        self.idx = {m: torch.empty((nq, k), dtype=torch.int64, device=dev) for m in self.metrics}
+        self.dist = {m: torch.empty((nq, k), dtype=torch.float32, device=dev) for m in self.metrics}
+        self.ws = torch.empty(bolt.topk_workspace_bytes(n, M, 1, k), dtype=torch.uint8, device=dev)
+        self.graphs = None
+        self.launches_per_step = 1 + len(self.metrics) * (2 + nq)
+        self.timing = []  # (start, end) event pairs around each top-k segment
+
+    def set_inputs(self, X, Q):
+        self.X.copy_(X)
+        self.Q.copy_(Q)
+
+    # The step in three kinds of segments, so that top-k launches can be timed
+    # by ordinary stream events recorded between graph replays.
+    def _pre(self):
+        bolt.encode(self.X, self.C, self.precision, out=self.codes)
+        for m in self.metrics:
+            a, b = self.quant[m]
+            bolt.build_luts(self.Q, self.C, m, a, b, out=self.luts[m])
+
+    def _topk(self, m):
+        for q in range(self.nq):
+            bolt.topk(self.codes, self.n, self.M, self.luts[m][q:q + 1], self.k, m,
+                      out_sums=self.sums[m][q:q + 1], out_idx=self.idx[m][q:q + 1], workspace=self.ws)
+
+    def _post(self):
+        for m in self.metrics:
+            a, b = self.quant[m]
+            bolt.dequantize(self.sums[m], a, b, out=self.dist[m])
+
+    def _segments(self):
+        return [self._pre] + [(lambda m=m: self._topk(m)) for m in self.metrics] + [self._post]
+
+    def run(self):
+        """Enqueue one step on the current stream (no host synchronization)."""
+        for seg in self._segments():
+            seg()
+
+    def capture(self):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run()  # warm-up outside capture: sets kernel attributes once
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        graphs = []
+        for seg in self._segments():
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, capture_error_mode="thread_local"):
+                seg()
+            graphs.append(g)
+        self.graphs = graphs
+        return graphs
+
+    def replay(self, timed=False):
+        if self.graphs is None:
+            self.capture()
+        self.graphs[0].replay()
+        for g in self.graphs[1:-1]:
+            if timed:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g.replay()
+                e1.record()
+                self.timing.append((e0, e1))
+            else:
+                g.replay()
+        self.graphs[-1].replay()
+
+    def topk_ms_per_launch(self):
+        """Mean duration of one top-k launch over the timed replays (call
+        after synchronizing)."""
+        if not self.timing:
+            return float("nan")
+        tot = sum(e0.elapsed_time(e1) for e0, e1 in self.timing)
+        return tot / (len(self.timing) * self.nq)
+
+    def run_from_host(self, X_host, Q_host, out_idx_host, out_dist_host):
+        """End to end: pinned host inputs -> device step -> host results."""
+        self.X.copy_(X_host, non_blocking=True)
+        self.Q.copy_(Q_host, non_blocking=True)
+        self.replay()
+        for j, m in enumerate(self.metrics):
+            out_idx_host[j].copy_(self.idx[m], non_blocking=True)
+            out_dist_host[j].copy_(self.dist[m], non_blocking=True)
+
+    def h2d_bytes(self):
+        return self.X.numel() * 4 + self.Q.numel() * 4
+
+    def d2h_bytes(self):
+        return len(self.metrics) * self.nq * self.k * (8 + 4)
