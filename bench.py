@@ -313,7 +313,7 @@ def run_reference(args, world, rank):
     vals = []
     desc = ""
     for i in range(args.warmup + args.steps):
-        v, work, desc = cpu_sample(cfg, X, Q, C, quant, rows_enc=20_000, q_sample=1)
+        v, work, desc = cpu_sample(cfg, X, Q, C, quant, rows_enc=100_000, q_sample=4)
         if i >= args.warmup:
             vals.append(v)
     v = float(np.median(vals))
@@ -409,7 +409,7 @@ def run_bolt(args, world, rank, local):
         import oracle
 
         Cn = C.cpu().numpy()
-        v, work, desc = cpu_sample(cfg, X, Q, Cn, quant)
+        v, work, desc = cpu_sample(cfg, X, Q, Cn, quant, rows_enc=cfg["n"], q_sample=200)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                                 "cpu_seconds": round(work, 2)}
         del oracle

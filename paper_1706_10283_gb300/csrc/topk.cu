@@ -268,7 +268,8 @@ __device__ int keep_if(uint64_t *keys, int cnt, uint32_t *wcnt, P pred) {
 
 // MT > 0 fixes the codebook count at compile time (fully unrolled lookups);
 // MT = 0 reads it from M.
-template <int WARPS, int MT>
+// BPI: code blocks per unit of work (one bulk copy, one loop iteration).
+template <int WARPS, int MT, int BPI>
 __global__ void __launch_bounds__(WARPS * 32, 1)
     topk_kernel(const uint32_t *__restrict__ codes, int64_t n, int32_t M, const uint8_t *__restrict__ luts,
                 int32_t k, int32_t metric, TopkWS ws, int stages, int cap, int hshift, int64_t blocks_per_cta,
@@ -279,7 +280,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     const int64_t q = blockIdx.y;
     const int G = gridDim.x, cta = blockIdx.x;
     if (MT > 0) M = MT;
-    const uint32_t stage_bytes = (uint32_t)M * kRowBytes;
+    const uint32_t blk_bytes = (uint32_t)M * kRowBytes;
+    const uint32_t stage_bytes = BPI * blk_bytes;
 
     uint8_t *p = smem;
     uint8_t *stage_base = p;
@@ -315,24 +317,29 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     fence_mbar_init();
     __syncthreads();
 
-    // Block indices fit in 32 bits (n < 2^31 vectors).
+    // Indices fit in 32 bits (n < 2^31 vectors).  Work units are BPI
+    // consecutive blocks; the CTA owns units [u_lo, u_hi).
     const uint32_t nb = (uint32_t)num_blocks(n);
-    const uint32_t b_lo = (uint32_t)min((int64_t)nb, (int64_t)cta * blocks_per_cta);
-    const uint32_t b_hi = (uint32_t)min((int64_t)nb, (int64_t)b_lo + blocks_per_cta);
+    const uint32_t nu = (nb + BPI - 1) / BPI;
+    const uint32_t u_lo = (uint32_t)min((int64_t)nu, (int64_t)cta * blocks_per_cta);
+    const uint32_t u_hi = (uint32_t)min((int64_t)nu, (int64_t)u_lo + blocks_per_cta);
     const uint32_t last_block = nb - 1;  // the only block that can hold vectors past n
     const uint32_t blk_words = (uint32_t)M * kRowWords;
     uint64_t *mybars = bars + warp * stages;
     uint8_t *mystage = stage_base + (size_t)warp * stages * stage_bytes;
+    // bytes of unit u (the last unit may hold fewer than BPI blocks)
+    auto unit_bytes = [&](uint32_t u) -> uint32_t { return min((uint32_t)BPI, nb - u * BPI) * blk_bytes; };
 
     // lane 0 of each warp is the producer of its ring
     uint32_t pending = 0;  // stages with a copy in flight (lane 0)
     uint32_t phase = 0;    // parity of the next completion of each stage (lane 0)
     if (lane == 0) {
         for (int s = 0; s < stages; ++s) {
-            const uint32_t b = b_lo + (uint32_t)s * WARPS + warp;
-            if (b < b_hi) {
-                mbar_arrive_expect_tx(&mybars[s], stage_bytes);
-                bulk_g2s(mystage + (size_t)s * stage_bytes, codes + (size_t)b * blk_words, stage_bytes, &mybars[s]);
+            const uint32_t u = u_lo + (uint32_t)s * WARPS + warp;
+            if (u < u_hi) {
+                const uint32_t bytes = unit_bytes(u);
+                mbar_arrive_expect_tx(&mybars[s], bytes);
+                bulk_g2s(mystage + (size_t)s * stage_bytes, codes + (size_t)u * BPI * blk_words, bytes, &mybars[s]);
                 pending |= 1u << s;
             }
         }
@@ -376,9 +383,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     const uint32_t smax = 255u * (uint32_t)M;  // largest possible sum
     const uint32_t smax2 = smax | (smax << 16);
     const bool swar = smax <= 0x7FFFu;  // sums fit in 15 bits (M <= 128)
-    const uint32_t gate = (uint32_t)(cap - WARPS * kBlockVecs);  // compact above this count
+    const uint32_t gate = (uint32_t)(cap - WARPS * BPI * kBlockVecs / 2);  // compact above this count
     // before the first compaction: compact as soon as a few blocks are in
-    const uint32_t early = min(gate, max((uint32_t)(2 * k), (uint32_t)(WARPS * kBlockVecs)));
+    const uint32_t early = min(gate, max((uint32_t)(2 * k), (uint32_t)(WARPS * BPI * kBlockVecs)));
     const uint32_t one = kMulOne;
     bool compacted = false;  // same value in every thread (set in cooperative())
 
@@ -455,15 +462,15 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         return __shfl_sync(0xFFFFFFFFu, f, 0);
     };
 
-    uint32_t st = 0, par = 0;  // stage and parity of this warp's current block
-    uint32_t j = 0;            // blocks done by this warp
+    uint32_t st = 0, par = 0;  // stage and parity of this warp's current unit
+    uint32_t j = 0;            // units done by this warp
     uint32_t refresh_j = 0xFFFFFFFFu;
-    for (uint32_t b = b_lo + warp;; b += WARPS, ++j) {
+    for (uint32_t u = u_lo + warp;; u += WARPS, ++j) {
         if (requests()) {
             const uint32_t f = cooperative();
             if (f & 1u) refresh_j = j + 2;  // refresh again once the other CTAs have published
         }
-        if (b >= b_hi || failed) break;
+        if (u >= u_hi || failed) break;
         if (!__all_sync(0xFFFFFFFFu, mbar_try_wait(&mybars[st], par))) {
             const bool ok = mbar_wait_bounded(&mybars[st], par, kWaitLimit);
             if (!__all_sync(0xFFFFFFFFu, ok)) {
@@ -472,23 +479,35 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             }
         }
         const uint32_t *words = reinterpret_cast<const uint32_t *>(mystage + (size_t)st * stage_bytes);
-        Acc8 acc;
-        acc.zero();
+        Acc8 acc[BPI];
+#pragma unroll
+        for (int h = 0; h < BPI; ++h) acc[h].zero();
+        // (a missing second block of the last unit reads stale stage data; its
+        // sums are masked out below)
         if (MT > 0) {
 #pragma unroll
-            for (int m = 0; m < MT; ++m) acc.add(prep_word(words[m * kRowWords + lane]), lut[m]);
+            for (int m = 0; m < MT; ++m) {
+                const uint4 t = lut[m];
+#pragma unroll
+                for (int h = 0; h < BPI; ++h) acc[h].add(prep_word(words[h * blk_words + m * kRowWords + lane]), t);
+            }
         } else {
 #pragma unroll 4
-            for (int m = 0; m < M; ++m) acc.add(prep_word(words[m * kRowWords + lane]), lut[m]);
+            for (int m = 0; m < M; ++m) {
+                const uint4 t = lut[m];
+#pragma unroll
+                for (int h = 0; h < BPI; ++h) acc[h].add(prep_word(words[h * blk_words + m * kRowWords + lane]), t);
+            }
         }
         __syncwarp();
         if (lane == 0) {
             pending &= ~(1u << st);
             phase ^= 1u << st;
-            const uint32_t b2 = b + (uint32_t)stages * WARPS;
-            if (b2 < b_hi) {
-                mbar_arrive_expect_tx(&mybars[st], stage_bytes);
-                bulk_g2s(mystage + (size_t)st * stage_bytes, codes + (size_t)b2 * blk_words, stage_bytes,
+            const uint32_t u2 = u + (uint32_t)stages * WARPS;
+            if (u2 < u_hi) {
+                const uint32_t bytes = unit_bytes(u2);
+                mbar_arrive_expect_tx(&mybars[st], bytes);
+                bulk_g2s(mystage + (size_t)st * stage_bytes, codes + (size_t)u2 * BPI * blk_words, bytes,
                          &mybars[st]);
                 pending |= 1u << st;
             }
@@ -497,39 +516,54 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             st = 0;
             par ^= 1u;
         }
-        uint32_t e_lo, o_lo, e_hi, o_hi;
-        acc.finish(e_lo, o_lo, e_hi, o_hi);
-        if (metric == BOLT_METRIC_DOT) {  // s' = 255*M - S in each 16-bit lane (no borrow)
-            e_lo = smax2 - e_lo;
-            o_lo = smax2 - o_lo;
-            e_hi = smax2 - e_hi;
-            o_hi = smax2 - o_hi;
-        }
-        const uint32_t v0 = b * kBlockVecs + 8u * lane;
-        const bool tail = b == last_block;
+        uint32_t pk[BPI][4];
         uint32_t thr = vmisc[1];
-        bool maybe = true;
-        if (swar && thr <= 0x7FFFu) {
-            // s' < 2^15: the top bit of (s' + 2^15 - thr) in each lane is clear
-            // exactly when s' < thr, with no borrow between lanes.
-            const uint32_t nt2 = 0u - (thr | (thr << 16));
-            const uint32_t d = imad(e_lo | 0x80008000u, one, nt2) & imad(o_lo | 0x80008000u, one, nt2) &
-                               imad(e_hi | 0x80008000u, one, nt2) & imad(o_hi | 0x80008000u, one, nt2);
-            maybe = (~d & 0x80008000u) != 0u;
+        bool maybe = false;
+        uint32_t v0[BPI];
+        bool tail[BPI], valid[BPI];
+#pragma unroll
+        for (int h = 0; h < BPI; ++h) {
+            const uint32_t b = u * BPI + h;
+            valid[h] = b <= last_block;
+            tail[h] = b == last_block;
+            v0[h] = b * kBlockVecs + 8u * lane;
+            uint32_t e_lo, o_lo, e_hi, o_hi;
+            acc[h].finish(e_lo, o_lo, e_hi, o_hi);
+            if (metric == BOLT_METRIC_DOT) {  // s' = 255*M - S in each 16-bit lane (no borrow)
+                e_lo = smax2 - e_lo;
+                o_lo = smax2 - o_lo;
+                e_hi = smax2 - e_hi;
+                o_hi = smax2 - o_hi;
+            }
+            bool mh = valid[h];
+            if (swar && thr <= 0x7FFFu) {
+                // s' < 2^15: the top bit of (s' + 2^15 - thr) in each lane is
+                // clear exactly when s' < thr, with no borrow between lanes.
+                const uint32_t nt2 = 0u - (thr | (thr << 16));
+                const uint32_t d = imad(e_lo | 0x80008000u, one, nt2) & imad(o_lo | 0x80008000u, one, nt2) &
+                                   imad(e_hi | 0x80008000u, one, nt2) & imad(o_hi | 0x80008000u, one, nt2);
+                mh = mh && (~d & 0x80008000u) != 0u;
+            }
+            if (tail[h]) mh = mh && v0[h] < (uint32_t)n;
+            maybe = maybe || mh;
+            const uint4 q4 = pack_sums(e_lo, o_lo, e_hi, o_hi);
+            pk[h][0] = q4.x;
+            pk[h][1] = q4.y;
+            pk[h][2] = q4.z;
+            pk[h][3] = q4.w;
         }
-        if (tail) maybe = maybe && v0 < (uint32_t)n;
         if (__any_sync(0xFFFFFFFFu, maybe)) {
-            const uint4 pk = pack_sums(e_lo, o_lo, e_hi, o_hi);
-            const uint32_t w4[4] = {pk.x, pk.y, pk.z, pk.w};
             for (int attempt = 0;; ++attempt) {
                 // One warp prefix sum places every lane's candidates; the slots
                 // are reserved with a compare-and-swap that never passes cap.
                 uint32_t cm = 0;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const uint32_t sp = (w4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
-                    if (sp < thr && (!tail || v0 + i < (uint32_t)n)) cm |= 1u << i;
-                }
+                for (int h = 0; h < BPI; ++h)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const uint32_t sp = (pk[h][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                        if (valid[h] && sp < thr && (!tail[h] || v0[h] + i < (uint32_t)n)) cm |= 1u << (8 * h + i);
+                    }
                 const uint32_t c = __popc(cm);
                 uint32_t incl = c;
 #pragma unroll
@@ -555,12 +589,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
                     base = __shfl_sync(0xFFFFFFFFu, base, 31);
                     uint32_t pos = base + incl - c;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        if (cm & (1u << i)) {
-                            const uint32_t sp = (w4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
-                            keys[pos++] = ((uint64_t)sp << 32) | (uint64_t)(v0 + i);
+                    for (int h = 0; h < BPI; ++h)
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            if (cm & (1u << (8 * h + i))) {
+                                const uint32_t sp = (pk[h][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                                keys[pos++] = ((uint64_t)sp << 32) | (uint64_t)(v0[h] + i);
+                            }
                         }
-                    }
                     break;
                 }
                 // Buffer full: compact with the whole CTA, then retry with the
@@ -690,7 +726,11 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int plan_topk(int64_t n, int32_t M, int32_t k, TopkPlan *plan) {
     BOLT_REQUIRE(k >= 1 && k <= kMaxK, BOLT_EUNSUPPORTED, "k=%d outside [1, %d]", k, kMaxK);
-    const size_t stage_bytes = (size_t)M * kRowBytes;
+    // Two blocks per unit of work for small M on large databases (amortizes
+    // per-unit overhead once every warp has many blocks to stream).
+    const int64_t blocks_per_warp = num_blocks(n) / ((int64_t)(device_sm_count() > 0 ? device_sm_count() : 1) * 16);
+    const int bpi = ((M == 8 || M == 16) && blocks_per_warp >= 16) ? 2 : 1;
+    const size_t stage_bytes = (size_t)bpi * M * kRowBytes;
     int warps = 16, stages = 0;
     for (warps = 16; warps >= 2; warps >>= 1) {
         stages = (int)(kStageBudget / (warps * stage_bytes));
@@ -698,28 +738,32 @@ int plan_topk(int64_t n, int32_t M, int32_t k, TopkPlan *plan) {
         if (stages >= 2) break;
     }
     BOLT_REQUIRE(stages >= 2, BOLT_EUNSUPPORTED, "M=%d too large for the top-k kernel", M);
-    const int cap = (k + 15) / 16 * 16 + 2 * warps * kBlockVecs;  // multiple of 16: keeps later regions aligned
+    // room for one unit of candidates per warp above the compaction gate;
+    // a multiple of 16 keeps the later shared-memory regions aligned
+    const int cap = (k + 15) / 16 * 16 + warps * bpi * kBlockVecs;
     int hshift = 0;
     while (((255 * M) >> hshift) >= kBins) ++hshift;
     const int64_t nb = num_blocks(n);
+    const int64_t nu = (nb + bpi - 1) / bpi;
     const size_t region = (size_t)warps * stages * stage_bytes + (size_t)cap * 8;
     const int64_t merge_keys = (int64_t)(region / 8);
     int64_t g = device_sm_count();
     if (g <= 0) g = 1;
-    const int64_t by_work = (nb + warps - 1) / warps;  // at least one full round per CTA
+    const int64_t by_work = (nu + warps - 1) / warps;  // at least one unit per warp
     if (g > by_work) g = by_work;
     if (g > merge_keys / k) g = merge_keys / k;  // the merge holds every CTA's list
     if (g < 1) g = 1;
     int64_t out_cap = merge_keys / g;  // candidates one CTA may hand to the merge (>= k)
     if (out_cap > 2 * k) out_cap = 2 * k;
     plan->warps = warps;
+    plan->bpi = bpi;
     plan->stages = stages;
     plan->grid = (int)g;
     plan->cap = cap;
     plan->hshift = hshift;
     plan->out_cap = (int)out_cap;
     plan->list_cap = (int)(g * out_cap);
-    plan->blocks_per_cta = nb > 0 ? (nb + g - 1) / g : 0;
+    plan->blocks_per_cta = nu > 0 ? (nu + g - 1) / g : 0;  // units per CTA
     plan->smem_bytes = region + align_up((size_t)M * 16, 16) + (size_t)warps * kMaxStages * 8 + kBins * 4 + 128 * 4;
     return BOLT_OK;
 }
@@ -746,11 +790,11 @@ TopkWS carve_topk_ws(void *ws, const TopkPlan &plan, int64_t nq, int32_t k) {
     return w;
 }
 
-template <int WARPS, int MT>
+template <int WARPS, int MT, int BPI>
 static int launch_w(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, int32_t k,
                     int32_t metric, uint16_t *out_sums, int64_t *out_idx, const TopkWS &w, const TopkPlan &plan,
                     cudaStream_t stream) {
-    auto kern = topk_kernel<WARPS, MT>;
+    auto kern = topk_kernel<WARPS, MT, BPI>;
     int rc = ensure_smem((const void *)kern, plan.smem_bytes);
     if (rc) return rc;
     dim3 grid(plan.grid, (unsigned)nq);
@@ -768,14 +812,14 @@ int launch_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts,
     const TopkWS w = carve_topk_ws(workspace, plan, nq, k);
 #define BOLT_TOPK_ARGS codes, n, M, luts, nq, k, metric, out_sums, out_idx, w, plan, stream
     if (plan.warps == 16) {
-        if (M == 8) return launch_w<16, 8>(BOLT_TOPK_ARGS);
-        if (M == 16) return launch_w<16, 16>(BOLT_TOPK_ARGS);
-        if (M == 32) return launch_w<16, 32>(BOLT_TOPK_ARGS);
-        return launch_w<16, 0>(BOLT_TOPK_ARGS);
+        if (M == 8) return plan.bpi == 2 ? launch_w<16, 8, 2>(BOLT_TOPK_ARGS) : launch_w<16, 8, 1>(BOLT_TOPK_ARGS);
+        if (M == 16) return plan.bpi == 2 ? launch_w<16, 16, 2>(BOLT_TOPK_ARGS) : launch_w<16, 16, 1>(BOLT_TOPK_ARGS);
+        if (M == 32) return launch_w<16, 32, 1>(BOLT_TOPK_ARGS);
+        return launch_w<16, 0, 1>(BOLT_TOPK_ARGS);
     }
-    if (plan.warps == 8) return launch_w<8, 0>(BOLT_TOPK_ARGS);
-    if (plan.warps == 4) return launch_w<4, 0>(BOLT_TOPK_ARGS);
-    return launch_w<2, 0>(BOLT_TOPK_ARGS);
+    if (plan.warps == 8) return launch_w<8, 0, 1>(BOLT_TOPK_ARGS);
+    if (plan.warps == 4) return launch_w<4, 0, 1>(BOLT_TOPK_ARGS);
+    return launch_w<2, 0, 1>(BOLT_TOPK_ARGS);
 #undef BOLT_TOPK_ARGS
 }
 

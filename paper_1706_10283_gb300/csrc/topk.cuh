@@ -9,13 +9,14 @@ constexpr int kBins = 4096;  // histogram bins over candidate sums
 
 struct TopkPlan {
     int warps;            // warps per CTA (16, 8, 4 or 2, by stage size)
+    int bpi;              // code blocks per unit of work (one bulk copy)
     int stages;           // TMA stages per warp
     int grid;             // CTAs per query
     int cap;              // candidate-buffer entries per CTA
     int hshift;           // histogram bin width 2^hshift
     int out_cap;          // candidates one CTA may append (k <= out_cap <= 2k)
     int list_cap;         // per-query candidate list capacity (grid * out_cap)
-    int64_t blocks_per_cta;
+    int64_t blocks_per_cta;  // units of work per CTA
     size_t smem_bytes;
 };
 

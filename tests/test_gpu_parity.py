@@ -142,6 +142,7 @@ def check_topk(torch, codes, luts, k, metric, workspace=None):
 
 @pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
 @pytest.mark.parametrize("n,M,k", [(5, 4, 10), (256, 8, 1), (1000, 8, 10), (10_003, 16, 100), (70_000, 16, 37),
+                                   (1539, 16, 10), (100_003, 16, 100), (25_603, 8, 64),
                                    (200_000, 8, 100), (50_000, 32, 1000), (20_000, 64, 50), (3000, 128, 20),
                                    (600, 256, 5)])
 def test_topk_bitexact(torch_cuda, metric, n, M, k):
