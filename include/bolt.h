@@ -133,6 +133,28 @@ int bolt_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts,
               int64_t *out_idx, void *workspace, int64_t workspace_bytes,
               void *stream);
 
+/* Allocation-free variant of bolt_topk (the paper has no counterpart: this is
+ * an interface for callers that may not allocate device memory during the
+ * call -- e.g. code issuing work while a CUDA graph is being captured under a
+ * strict capture mode, latency-critical serving loops that keep allocator
+ * calls off the request path, or embedders whose own allocator owns the GPU
+ * heap).  Same arguments, results and order as bolt_topk, without the
+ * workspace: the scratch space is a 4 MiB array compiled into libbolt.so,
+ * which every GPU that loads the library keeps until the process exits.
+ *  - The call makes no cudaMalloc/cudaFree or other allocation; it zeroes the
+ *    parts of the array that must start at zero with cudaMemsetAsync.
+ *  - Requests whose scratch need (bolt_topk_workspace_bytes(n, M, nq, k))
+ *    exceeds 4 MiB fail with BOLT_ENOMEM and a message; split the queries.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture on that device.
+ *  - All calls share the one array: calls that may overlap on the GPU (other
+ *    streams, other host threads) race and give wrong results; serialize them
+ *    (one stream, or events). */
+int bolt_topk_noalloc(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts,
+                      int64_t nq, int32_t k, int32_t metric, uint16_t *out_sums,
+                      int64_t *out_idx, void *stream);
+
 /* ---------------------------------------------------------------- dequantize
  * Sec. 3.2: the per-table reconstructions beta_m/a + b_m sum to
  * S * (1/a) + sum_m b_m.  Host helper (fp64, no GPU): inv_a =

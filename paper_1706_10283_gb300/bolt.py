@@ -45,6 +45,8 @@ _SIGS = {
     "bolt_topk_workspace_bytes": ([C.c_int64, C.c_int32, C.c_int64, C.c_int32], C.c_int64),
     "bolt_topk": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
                    C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
+    "bolt_topk_noalloc": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32,
+                           C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_dequant_params": ([C.c_float, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_dequantize": ([C.c_void_p, C.c_int64, C.c_float, C.c_float, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_approx_matmul": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,

@@ -30,6 +30,8 @@
 // finish (atomic ticket) finds the final bound bin from the histogram,
 // gathers the few candidates at or below it into shared memory, selects the
 // exact k smallest keys, sorts them and writes the result.
+#include <mutex>
+
 #include "scan_core.cuh"
 #include "topk.cuh"
 
@@ -870,3 +872,64 @@ int bolt_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, i
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free variant
+// Some callers cannot allocate device memory at call time: code running while
+// a CUDA graph is being captured with a strict capture mode, real-time or
+// serving loops that forbid allocator calls (and their latency spikes) on the
+// request path, and embedders whose own memory manager owns the device heap.
+// bolt_topk_noalloc serves them: its scratch space is a fixed array compiled
+// into the library, so the call itself never allocates or frees.
+namespace bolt {
+
+constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;  // 4 MiB, held by every GPU that loads the library
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (host code may not use the symbol itself as a device pointer).
+static int noalloc_scratch(void **ptr) {
+    static std::mutex mu;
+    static void *addr[64] = {nullptr};
+    int dev = 0;
+    BOLT_CUDA(cudaGetDevice(&dev));
+    BOLT_REQUIRE(dev >= 0 && dev < 64, BOLT_EUNSUPPORTED, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (addr[dev] == nullptr) {
+        void *p = nullptr;
+        BOLT_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        addr[dev] = p;
+    }
+    *ptr = addr[dev];
+    return BOLT_OK;
+}
+
+}  // namespace bolt
+
+extern "C" int bolt_topk_noalloc(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq,
+                                 int32_t k, int32_t metric, uint16_t *out_sums, int64_t *out_idx, void *stream) {
+    bolt::clear_error();
+    int rc = bolt::check_nm(n, M);
+    if (rc) return rc;
+    BOLT_REQUIRE(nq >= 0, BOLT_EINVAL, "nq=%lld < 0", (long long)nq);
+    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT, BOLT_EINVAL, "bad metric %d", metric);
+    bolt::TopkPlan plan;
+    rc = bolt::plan_topk(n, M, k, &plan);
+    if (rc) return rc;
+    if (nq == 0) return BOLT_OK;
+    BOLT_REQUIRE(luts && out_sums && out_idx && (codes || n == 0), BOLT_EINVAL, "null pointer");
+    BOLT_REQUIRE(bolt::aligned(luts, 16) && (n == 0 || bolt::aligned(codes, 16)), BOLT_EINVAL,
+                 "codes and luts must be 16-byte aligned");
+    const int64_t need = bolt::topk_workspace_bytes(plan, nq, k);
+    BOLT_REQUIRE(need <= (int64_t)bolt::kNoAllocScratchBytes, BOLT_ENOMEM,
+                 "bolt_topk_noalloc: %lld queries with k=%d need %lld bytes of scratch, more than its fixed "
+                 "%lld-byte array; use fewer queries per call or bolt_topk",
+                 (long long)nq, k, (long long)need, (long long)bolt::kNoAllocScratchBytes);
+    void *scratch = nullptr;
+    rc = bolt::noalloc_scratch(&scratch);
+    if (rc) return rc;
+    // launch_topk zeroes the per-query header and histograms (cudaMemsetAsync)
+    // before the kernel; the candidate lists need no clearing.
+    return bolt::launch_topk(codes, n, M, luts, nq, k, metric, out_sums, out_idx, scratch, plan,
+                             (cudaStream_t)stream);
+}
