@@ -69,8 +69,151 @@ __global__ void __launch_bounds__(256) encode_fp32_kernel(const float *__restric
     }
 }
 
+// ------------------------------------------------------------------ staged fp32 encoder
+// Tiles of 32 rows are copied row by row (1-D bulk copies, 16-byte aligned
+// rows) into shared memory with a row stride of an odd number of 16-byte
+// units, so the 32 lanes of a warp (lane = row) read their subvectors with
+// conflict-free 16-byte loads.  Warp w handles codebooks w, w + 8, ...; the 16
+// centroid values of one dim are one broadcast read of the transposed
+// centroid copy.  Two centroids are evaluated per packed fp32x2 instruction:
+// each half is the same IEEE round-to-nearest operation as the scalar
+// canonical order, so the codes are unchanged.
+constexpr int kEncRows = 32;
+constexpr int kEncThreads = 256;
+
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+    return (uint64_t)__float_as_uint(lo) | ((uint64_t)__float_as_uint(hi) << 32);
+}
+
+int enc_row_stride(int J) {  // floats per shared-memory row
+    int units = J / 4 + 1;
+    if ((units & 1) == 0) ++units;
+    return units * 4;
+}
+
+__global__ void __launch_bounds__(kEncThreads) encode_staged_kernel(const float *__restrict__ X, int64_t n, int32_t J,
+                                                                    int32_t M, const float *__restrict__ C,
+                                                                    uint32_t *__restrict__ codes, int row_stride) {
+    extern __shared__ __align__(128) uint8_t esmem[];
+    const int s = J / M;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *cs = reinterpret_cast<float *>(esmem);                       // [M][s][16]
+    float *xbuf = cs + (size_t)J * kK;                                   // 2 x [32][row_stride]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(xbuf + 2 * kEncRows * (size_t)row_stride);
+    for (int i = tid; i < J * kK; i += kEncThreads) {
+        const int j = i % s, k = (i / s) % kK, m = i / (s * kK);
+        cs[((size_t)m * s + j) * kK + k] = C[i];
+    }
+    if (tid < 2) mbar_init(&bars[tid], 1);
+    fence_mbar_init();
+    __syncthreads();
+
+    const int64_t ntiles = (n + kEncRows - 1) / kEncRows;
+    const uint32_t row_bytes = (uint32_t)J * 4u;
+    auto issue = [&](int64_t t, int buf) {  // warp 0: one bulk copy per valid row
+        const int64_t r0 = t * kEncRows;
+        const int rows = (int)min((int64_t)kEncRows, n - r0);
+        if (lane == 0) mbar_arrive_expect_tx(&bars[buf], (uint32_t)rows * row_bytes);
+        __syncwarp();
+        if (lane < rows)
+            bulk_g2s(xbuf + ((size_t)buf * kEncRows + lane) * row_stride, X + (r0 + lane) * J, row_bytes, &bars[buf]);
+    };
+    int64_t t = blockIdx.x;
+    if (warp == 0) {
+        if (t < ntiles) issue(t, 0);
+        if (t + gridDim.x < ntiles) issue(t + gridDim.x, 1);
+    }
+    uint32_t parbits = 0u;  // bit b: parity of buffer b's next completion
+    for (int buf = 0; t < ntiles; t += gridDim.x, buf ^= 1) {
+        const bool ok = mbar_wait_bounded(&bars[buf], (parbits >> buf) & 1u, 1000000000ull);
+        parbits ^= 1u << buf;
+        const int64_t r0 = t * kEncRows;
+        const bool valid = r0 + lane < n;
+        const float *xr = xbuf + ((size_t)buf * kEncRows + lane) * row_stride;
+        for (int m = warp; m < M; m += kEncThreads / 32) {
+            uint64_t acc[8];
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) acc[k2] = 0ull;
+            const float4 *cm = reinterpret_cast<const float4 *>(cs + (size_t)m * s * kK);
+            for (int j = 0; j < s; ++j) {
+                const float xj = xr[m * s + j];
+                const uint64_t x2 = f2_pack(xj, xj);
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    const float4 c4 = cm[j * 4 + k4];
+                    uint64_t t2 = f2_sub(x2, f2_pack(c4.x, c4.y));
+                    acc[2 * k4] = f2_fma(t2, t2, acc[2 * k4]);
+                    t2 = f2_sub(x2, f2_pack(c4.z, c4.w));
+                    acc[2 * k4 + 1] = f2_fma(t2, t2, acc[2 * k4 + 1]);
+                }
+            }
+            float best = __uint_as_float((uint32_t)acc[0]);
+            uint32_t code = 0;
+#pragma unroll
+            for (int k = 1; k < kK; ++k) {
+                const float d = __uint_as_float((uint32_t)(acc[k >> 1] >> (32 * (k & 1))));
+                if (d < best) {  // strict: ties keep the lower index
+                    best = d;
+                    code = (uint32_t)k;
+                }
+            }
+            if (!valid || !ok) code = 0;
+            uint32_t word = code << (4 * (lane & 7));
+            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
+            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
+            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
+            if ((lane & 7) == 0) {
+                const int64_t v = r0 + lane;  // first of 8 vectors; r0 is a multiple of 32
+                codes[((v >> 8) * M + m) * kRowWords + ((v & 255) >> 3)] = word;
+            }
+        }
+        if (t == ntiles - 1) {
+            // words of the last block past the last tile hold padding vectors: code 0
+            const int64_t v_end = r0 + kEncRows;
+            const int w_end = (int)((v_end & 255) >> 3);
+            if (w_end != 0)
+                for (int m = warp; m < M; m += kEncThreads / 32)
+                    for (int w = w_end + lane; w < kRowWords; w += 32)
+                        codes[(((v_end - 1) >> 8) * M + m) * kRowWords + w] = 0u;
+        }
+        __syncthreads();  // every warp is done with this buffer
+        if (warp == 0 && t + 2 * (int64_t)gridDim.x < ntiles) issue(t + 2 * (int64_t)gridDim.x, buf);
+    }
+}
+
 int launch_encode_fp32(const float *X, int64_t n, int32_t J, int32_t M, const float *C, uint8_t *codes,
                        cudaStream_t stream) {
+    if (J % 4 == 0 && aligned(X, 16)) {
+        const int64_t ntiles = (n + kEncRows - 1) / kEncRows;
+        if (ntiles == 0) return BOLT_OK;
+        const int rs = enc_row_stride(J);
+        const size_t smem = (size_t)J * kK * 4 + 2 * (size_t)kEncRows * rs * 4 + 2 * 8;
+        if (smem <= 220 * 1024) {
+            int rc = ensure_smem((const void *)encode_staged_kernel, smem);
+            if (rc) return rc;
+            int64_t grid = ntiles;
+            const int64_t cap = (int64_t)device_sm_count() * 2;
+            if (cap > 0 && grid > cap) grid = cap;
+            encode_staged_kernel<<<(int)grid, kEncThreads, smem, stream>>>(X, n, J, M, C,
+                                                                           reinterpret_cast<uint32_t *>(codes), rs);
+            return check_launch("encode_staged_kernel");
+        }
+    }
+    return launch_encode_simple(X, n, J, M, C, codes, stream);
+}
+
+int launch_encode_simple(const float *X, int64_t n, int32_t J, int32_t M, const float *C, uint8_t *codes,
+                         cudaStream_t stream) {
     const int64_t nb = num_blocks(n);
     if (nb == 0) return BOLT_OK;
     const size_t smem = (size_t)J * kK * sizeof(float);

@@ -5,6 +5,10 @@
 
 namespace bolt {
 
+// Staged (bulk-copied, shared-memory) kernel when J % 4 == 0, else the
+// simple one-vector-per-thread kernel.
+int launch_encode_simple(const float *X, int64_t n, int32_t J, int32_t M, const float *C, uint8_t *codes,
+                         cudaStream_t stream);
 int launch_encode_fp32(const float *X, int64_t n, int32_t J, int32_t M, const float *C, uint8_t *codes,
                        cudaStream_t stream);
 

@@ -45,7 +45,8 @@ def problem(n, J, M, seed, kind="mixture", nq=5):
 
 
 SHAPES = [(10_000, 32, 8, "iid"), (1_037, 128, 16, "mixture"), (513, 24, 4, "mixture"), (300, 64, 64, "mixture"),
-          (257, 16, 1, "mixture"), (40, 256, 32, "mixture"), (5, 8, 2, "iid")]
+          (257, 16, 1, "mixture"), (40, 256, 32, "mixture"), (5, 8, 2, "iid"), (1000, 6, 3, "iid"),
+          (3000, 512, 32, "mixture")]
 
 
 # ------------------------------------------------------------------ layout
