@@ -101,11 +101,44 @@ int enc_row_stride(int J) {  // floats per shared-memory row
     return units * 4;
 }
 
+// 16 canonical distances of one subvector, two centroids per fp32x2 op.
+// SC > 0: compile-time subspace size (a multiple of 4; 16-byte loads, full
+// unroll); SC = 0: runtime size s.
+template <int SC>
+__device__ __forceinline__ void subspace_dists(const float *xr, const float4 *cm, int s, uint64_t (&acc)[8]) {
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) acc[k2] = 0ull;
+    auto step = [&](float xj, int j) {
+        const uint64_t x2 = f2_pack(xj, xj);
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+            const float4 c4 = cm[j * 4 + k4];
+            uint64_t t2 = f2_sub(x2, f2_pack(c4.x, c4.y));
+            acc[2 * k4] = f2_fma(t2, t2, acc[2 * k4]);
+            t2 = f2_sub(x2, f2_pack(c4.z, c4.w));
+            acc[2 * k4 + 1] = f2_fma(t2, t2, acc[2 * k4 + 1]);
+        }
+    };
+    if (SC > 0) {
+#pragma unroll
+        for (int j4 = 0; j4 < SC / 4; ++j4) {
+            const float4 x4 = reinterpret_cast<const float4 *>(xr)[j4];
+            step(x4.x, 4 * j4 + 0);
+            step(x4.y, 4 * j4 + 1);
+            step(x4.z, 4 * j4 + 2);
+            step(x4.w, 4 * j4 + 3);
+        }
+    } else {
+        for (int j = 0; j < s; ++j) step(xr[j], j);
+    }
+}
+
+template <int SC>
 __global__ void __launch_bounds__(kEncThreads) encode_staged_kernel(const float *__restrict__ X, int64_t n, int32_t J,
                                                                     int32_t M, const float *__restrict__ C,
                                                                     uint32_t *__restrict__ codes, int row_stride) {
     extern __shared__ __align__(128) uint8_t esmem[];
-    const int s = J / M;
+    const int s = SC > 0 ? SC : J / M;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *cs = reinterpret_cast<float *>(esmem);                       // [M][s][16]
     float *xbuf = cs + (size_t)J * kK;                                   // 2 x [32][row_stride]
@@ -142,21 +175,7 @@ __global__ void __launch_bounds__(kEncThreads) encode_staged_kernel(const float 
         const float *xr = xbuf + ((size_t)buf * kEncRows + lane) * row_stride;
         for (int m = warp; m < M; m += kEncThreads / 32) {
             uint64_t acc[8];
-#pragma unroll
-            for (int k2 = 0; k2 < 8; ++k2) acc[k2] = 0ull;
-            const float4 *cm = reinterpret_cast<const float4 *>(cs + (size_t)m * s * kK);
-            for (int j = 0; j < s; ++j) {
-                const float xj = xr[m * s + j];
-                const uint64_t x2 = f2_pack(xj, xj);
-#pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) {
-                    const float4 c4 = cm[j * 4 + k4];
-                    uint64_t t2 = f2_sub(x2, f2_pack(c4.x, c4.y));
-                    acc[2 * k4] = f2_fma(t2, t2, acc[2 * k4]);
-                    t2 = f2_sub(x2, f2_pack(c4.z, c4.w));
-                    acc[2 * k4 + 1] = f2_fma(t2, t2, acc[2 * k4 + 1]);
-                }
-            }
+            subspace_dists<SC>(xr + m * s, reinterpret_cast<const float4 *>(cs + (size_t)m * s * kK), s, acc);
             float best = __uint_as_float((uint32_t)acc[0]);
             uint32_t code = 0;
 #pragma unroll
@@ -199,13 +218,16 @@ int launch_encode_fp32(const float *X, int64_t n, int32_t J, int32_t M, const fl
         const int rs = enc_row_stride(J);
         const size_t smem = (size_t)J * kK * 4 + 2 * (size_t)kEncRows * rs * 4 + 2 * 8;
         if (smem <= 220 * 1024) {
-            int rc = ensure_smem((const void *)encode_staged_kernel, smem);
+            const int sv = J / M;
+            auto kern = sv == 4 ? encode_staged_kernel<4>
+                        : sv == 8 ? encode_staged_kernel<8>
+                        : sv == 16 ? encode_staged_kernel<16> : encode_staged_kernel<0>;
+            int rc = ensure_smem((const void *)kern, smem);
             if (rc) return rc;
             int64_t grid = ntiles;
             const int64_t cap = (int64_t)device_sm_count() * 2;
             if (cap > 0 && grid > cap) grid = cap;
-            encode_staged_kernel<<<(int)grid, kEncThreads, smem, stream>>>(X, n, J, M, C,
-                                                                           reinterpret_cast<uint32_t *>(codes), rs);
+            kern<<<(int)grid, kEncThreads, smem, stream>>>(X, n, J, M, C, reinterpret_cast<uint32_t *>(codes), rs);
             return check_launch("encode_staged_kernel");
         }
     }
