@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--nq", type=int, default=None, help="override query count (profiling runs)")
     ap.add_argument("--no-aux", action="store_true", help="skip the large-N and encode side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["topk1m", "topk50m", "encode10m"], default=None,
+    ap.add_argument("--only", choices=["topk1m", "topk50m", "encode10m", "encode10m_tc"], default=None,
                     help="profiling run: set up one workload and launch only its kernel a few times")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--graph-reps", type=int, default=0, help="also time graph replays of the launches")
@@ -273,23 +273,43 @@ def encode_10m():
     C = bolt.fit_codebooks(sub, M, 8, synth.kmeans_init_rows(100_000, 0))
     codes = torch.empty(bolt.codes_bytes(n, M), dtype=torch.uint8, device="cuda")
     out = {}
-    for name, prec in (("fp32", bolt.PREC_FP32),):
+    hbm_peak, _ = peaks()
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    codes_tc = torch.empty_like(codes)
+    for name, prec, dst in (("fp32", bolt.PREC_FP32, codes), ("bf16_tensor_core_recheck", bolt.PREC_BF16_RECHECK,
+                                                                codes_tc)):
         for _ in range(2):
-            bolt.encode(X, C, prec, out=codes)
+            bolt.encode(X, C, prec, out=dst, n_rechecked=cnt)
         torch.cuda.synchronize()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         reps = 5
         ev[0].record()
         for _ in range(reps):
-            bolt.encode(X, C, prec, out=codes)
+            bolt.encode(X, C, prec, out=dst, n_rechecked=cnt)
         ev[1].record()
         torch.cuda.synchronize()
         ms = ev[0].elapsed_time(ev[1]) / reps
+        gbs = (n * J * 4 + n * M / 2) / (ms * 1e-3) / 1e9
         out[name] = {"ms": round(ms, 4), "input_GBps": round(n * J * 4 / (ms * 1e-3) / 1e9, 1),
-                     "vectors_per_s": n / (ms * 1e-3)}
-    del X, codes
+                     "vectors_per_s": n / (ms * 1e-3), "hbm_frac": round(gbs / hbm_peak, 4),
+                     "rechecked_pairs": int(cnt.item()), "recheck_rate": round(int(cnt.item()) / (n * M), 4)}
+    same = bool(torch.equal(codes, codes_tc))
+    # precision report on a sample of rows: codes vs the fp64 argmin, and the
+    # reconstruction error of the fp32 codes vs the fp64 codes
+    import oracle
+
+    rows = 20_000
+    Xs = X[:rows].cpu().numpy()
+    Cn = C.cpu().numpy()
+    c64 = oracle.encode(Xs, Cn, precision="f64")
+    c32 = bolt.unpack_codes(codes_tc[:bolt.codes_bytes(rows, M)], rows, M).cpu().numpy()
+    mse = lambda cc: float(np.mean(np.sum((Xs.astype(np.float64) - oracle.decode(cc, Cn)) ** 2, axis=1)))  # noqa
+    del X, codes, codes_tc
     torch.cuda.empty_cache()
-    return {"workload": "encode_10m: 10,000,000 x 256 fp32 mixture, M=32", **out}
+    return {"workload": "encode_10m: 10,000,000 x 256 fp32 mixture, M=32", **out,
+            "tensor_core_codes_equal_fp32": same,
+            "sample_rows": rows, "mismatch_rate_vs_fp64": float(np.mean(c32 != c64)),
+            "mse_fp32_codes": mse(c32), "mse_fp64_codes": mse(c64)}
 
 
 # ------------------------------------------------------------------ arms
@@ -445,13 +465,14 @@ def run_only(args):
 
     torch.cuda.set_device(0)
     bolt.lib()
-    if args.only == "encode10m":
+    if args.only in ("encode10m", "encode10m_tc"):
         cfg = synth.CONFIGS["encode_10m"]
         n, J, M = 2_000_000, cfg["J"], cfg["M"]  # 2 GB of fp32 input: > L2, small for ncu
         X = synth.mixture_torch(n, J, seed=0)
         C = bolt.fit_codebooks(X[:100_000].contiguous(), M, 4, synth.kmeans_init_rows(100_000, 0))
         codes = torch.empty(bolt.codes_bytes(n, M), dtype=torch.uint8, device="cuda")
-        fn = lambda: bolt.encode(X, C, bolt.PREC_FP32, out=codes)  # noqa: E731
+        prec = bolt.PREC_BF16_RECHECK if args.only == "encode10m_tc" else bolt.PREC_FP32
+        fn = lambda: bolt.encode(X, C, prec, out=codes)  # noqa: E731
     else:
         cfg = workload(8)
         X, Q, Xd, Qd, C, quant = prepare(cfg, 0)

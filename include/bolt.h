@@ -86,13 +86,18 @@ int bolt_unpack_codes(const uint8_t *blocked, int64_t n, int32_t M,
  * dims, in dim order, of acc = fmaf(t, t, acc), t = x_j - c_j, from 0; ties
  * go to the lowest k.
  * precision BOLT_PREC_FP32 computes exactly that.  BOLT_PREC_BF16_RECHECK
- * scores ||c||^2 - 2 x.c on tcgen05 tensor cores in bf16 with fp32
- * accumulation and re-evaluates the canonical fp32 distances of every
- * centroid within a rigorous error margin of the best score, so its codes
- * equal BOLT_PREC_FP32's.
+ * scores ||c||^2 - 2 x.c on tcgen05 tensor cores: x and c are each split
+ * into a bf16 high part and a bf16 residual, three bf16 MMAs (hi.hi, hi.lo,
+ * lo.hi) accumulate in fp32, and every centroid whose score lies within a
+ * rigorous error margin of the best is re-evaluated with the canonical fp32
+ * distance, so its codes equal BOLT_PREC_FP32's.  It needs J % 32 == 0 and
+ * s = J / M in {4, 8, 16, 32}; other shapes run the fp32 kernel instead.
  * X: n x J fp32 (16-byte aligned); codes: blocked, bolt_codes_bytes(n, M).
  * n_rechecked (nullable, device int64): set to the number of (vector,
- * subspace) pairs that took the fp32 re-check (0 for BOLT_PREC_FP32). */
+ * subspace) pairs that took the fp32 re-check (0 for BOLT_PREC_FP32), or
+ * to -1 if the tensor-core kernel gave up waiting on its own copies; the
+ * codes are then invalid (the launch itself is asynchronous, so this is
+ * the only report of that failure). */
 int bolt_encode(const float *X, int64_t n, int32_t J, int32_t M,
                 const float *centroids, int32_t precision, uint8_t *codes,
                 int64_t *n_rechecked, void *stream);

@@ -88,6 +88,46 @@ def test_encode_adversarial_ties(torch_cuda):
     np.testing.assert_array_equal(decode_blocked(got.cpu().numpy(), len(X), 4), oracle.encode(X, C_))
 
 
+TC_SHAPES = [(10_000, 32, 8), (1_037, 128, 16), (40, 256, 32), (513, 64, 4), (777, 64, 2), (3000, 512, 32),
+             (1, 128, 16), (129, 128, 16), (257, 128, 16), (20_000, 256, 32)]
+
+
+@pytest.mark.parametrize("n,J,M", TC_SHAPES)
+def test_encode_tensor_core_bitexact(torch_cuda, n, J, M):
+    """bf16 tensor-core scores + fp32 re-check give the canonical fp32 codes."""
+    torch = torch_cuda
+    X, _, C_ = problem(n, J, M, 4)
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    got = bolt.encode(dev(torch, X), dev(torch, C_), bolt.PREC_BF16_RECHECK, n_rechecked=cnt)
+    np.testing.assert_array_equal(decode_blocked(got.cpu().numpy(), n, M), oracle.encode(X, C_))
+    assert 0 <= int(cnt.item()) <= n * M
+
+
+@pytest.mark.parametrize("scale", [1e-3, 1.0, 1e3])
+def test_encode_tensor_core_near_ties(torch_cuda, scale):
+    """Points at and near the midpoints between centroids, duplicated
+    centroids and exact centroid hits: the re-check must resolve every one
+    exactly as the fp32 encoder does."""
+    torch = torch_cuda
+    rng = np.random.default_rng(int(scale * 7) + 1)
+    M, s = 16, 8
+    C_ = (rng.standard_normal((M, 16, s)) * scale).astype(np.float32)
+    C_[:, 5] = C_[:, 2]  # duplicate
+    n = 4096
+    a = rng.integers(0, 16, (n, M))
+    b = rng.integers(0, 16, (n, M))
+    w = rng.uniform(0.45, 0.55, (n, M, 1))
+    eps = rng.choice([0.0, 1e-7, -1e-7, 1e-5, -1e-5, 1e-3], (n, M, 1))
+    sub = np.stack([C_[m, a[:, m]] * (w[:, m] + eps[:, m]) + C_[m, b[:, m]] * (1 - w[:, m] - eps[:, m])
+                    for m in range(M)], axis=1)
+    sub[::5] = np.stack([C_[m, a[::5, m]] for m in range(M)], axis=1)  # exact hits
+    X = sub.reshape(n, M * s).astype(np.float32)
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    got = bolt.encode(dev(torch, X), dev(torch, C_), bolt.PREC_BF16_RECHECK, n_rechecked=cnt)
+    np.testing.assert_array_equal(decode_blocked(got.cpu().numpy(), n, M), oracle.encode(X, C_))
+    assert int(cnt.item()) > 0
+
+
 # ------------------------------------------------------------------ LUT
 @pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
 @pytest.mark.parametrize("n,J,M,kind", SHAPES[:5])
