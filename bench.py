@@ -15,6 +15,9 @@ Also reported in the same JSON line:
   large_n_scan  one L2 top-100 query over a 50,000,000-vector database
                 (400 MB of codes, larger than L2) against the HBM roofline,
   encode_10m    encode of 10,000,000 x 256 fp32 (M = 32) in input GB/s,
+  batched_collections  64 collections of uneven size scanned in one
+                persistent launch, against one launch per collection and
+                one launch per query,
   cpu_baseline  the CPU oracle timed on a bounded sample of the same workload.
 
 ``--impl reference`` times the CPU oracle (the only reference this method
@@ -51,10 +54,11 @@ def parse():
     ap.add_argument("--nq", type=int, default=None, help="override query count (profiling runs)")
     ap.add_argument("--no-aux", action="store_true", help="skip the large-N and encode side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["topk1m", "topk50m", "encode10m", "encode10m_tc"], default=None,
+    ap.add_argument("--only", choices=["topk1m", "topk50m", "encode10m", "encode10m_tc", "batch"], default=None,
                     help="profiling run: set up one workload and launch only its kernel a few times")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--graph-reps", type=int, default=0, help="also time graph replays of the launches")
+    ap.add_argument("--collections", type=int, default=64, help="--only batch: first N collections")
     return ap.parse_args()
 
 
@@ -312,6 +316,121 @@ def encode_10m():
             "mse_fp32_codes": mse(c32), "mse_fp64_codes": mse(c64)}
 
 
+def collections_setup(count=64):
+    """The multi-collection batch on the GPU: per collection the seeded
+    mixture data, a GPU fit (8 k-means iterations on up to 50,000 rows, the
+    quantizer on 256 training rows), codes, query tables (L2 for even, dot
+    for odd collections) and an output matrix."""
+    import torch
+
+    from paper_1706_10283_gb300 import bolt, synth
+
+    specs = synth.collections(seed=3)[:count]
+    out = []
+    for ci, sp in enumerate(specs):
+        n, J, M, nq = sp["n"], sp["J"], sp["M"], sp["nq"]
+        metric = ci % 2
+        X = synth.mixture_torch(n, J, sp["data_seed"])
+        nf = min(n, 50_000)
+        Qtr = X[torch.from_numpy(synth.train_query_rows(n, sp["data_seed"])).cuda()].contiguous()
+        C, a, b = bolt.fit_codebooks(X[:nf].contiguous(), M, 8, synth.kmeans_init_rows(nf, sp["data_seed"]),
+                                     Qtrain=Qtr, metric=metric)
+        codes = bolt.encode(X, C)
+        del X, Qtr
+        Q = synth.mixture_torch(nq, J, sp["query_seed"])
+        luts = bolt.build_luts(Q, C, metric, a, b)
+        sums = torch.empty((nq, bolt.sums_ld(n)), dtype=torch.int16, device="cuda").view(torch.uint16)
+        out.append(dict(n=n, J=J, M=M, nq=nq, codes=codes, luts=luts, sums=sums))
+    torch.cuda.synchronize()
+    return out
+
+
+def _graph_ms(fn, reps):
+    """Device time of one call of fn, captured once in a CUDA graph and
+    replayed `reps` times between two events."""
+    import torch
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn(s)  # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        fn(s)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def batched_collections():
+    """64 collections (N log-uniform in [1e3, 2e6], J in {64,128,256}, M in
+    {8,16,32}, 1..256 queries each) scanned three ways, each captured in a
+    CUDA graph: one persistent batched launch (autotuned tiles), one
+    bolt_scan_l2 launch per collection, and one launch per query."""
+    import torch
+
+    from paper_1706_10283_gb300 import alu_peak, bolt
+
+    batch = collections_setup()
+    dists = sum(c["n"] * c["nq"] for c in batch)
+    lookups = sum(c["n"] * c["nq"] * c["M"] for c in batch)
+    plan = bolt.BatchPlan([(c["codes"], c["n"], c["M"], c["luts"], c["sums"]) for c in batch])
+    t0 = time.perf_counter()
+    tune_ms = plan.autotune()
+    tune_s = time.perf_counter() - t0
+    batched_ms = _graph_ms(lambda s: plan.run(stream=s), reps=10)
+    plain = [torch.empty((c["nq"], c["n"]), dtype=torch.int16, device="cuda").view(torch.uint16) for c in batch]
+
+    def per_collection(s):
+        for c, o in zip(batch, plain):
+            bolt.scan_l2(c["codes"], c["n"], c["M"], c["luts"], out=o, stream=s)
+
+    def per_query(s):
+        for c, o in zip(batch, plain):
+            for q in range(c["nq"]):
+                bolt.scan_l2(c["codes"], c["n"], c["M"], c["luts"][q:q + 1], out=o[q:q + 1], stream=s)
+
+    coll_ms = _graph_ms(per_collection, reps=5)
+    query_ms = _graph_ms(per_query, reps=2)
+    plan.run()
+    torch.cuda.synchronize()
+    same = all(torch.equal(c["sums"].view(torch.int16)[:, :c["n"]], o.view(torch.int16)) for c, o in zip(batch, plain))
+    peak = alu_peak.lookups_per_s()
+    tuning = plan.tuning()
+    by_m = {}
+    for c, (qt, upw) in zip(batch, tuning):
+        by_m[str(c["M"])] = {"qt_max": qt, "units_per_warp": upw}
+    res = {"workload": "64 collections, N log-uniform in [1e3, 2e6] (%d vectors), J in {64,128,256}, "
+                       "M in {8,16,32}, 1-256 queries each (%d queries)" % (sum(c["n"] for c in batch),
+                                                                            sum(c["nq"] for c in batch)),
+           "distances_per_batch": dists, "lookups_per_batch": lookups,
+           "batched": {"ms": round(batched_ms, 4), "distances_per_s": dists / (batched_ms * 1e-3),
+                       "launches": 1, "tiles_by_M": by_m, "autotune_s": round(tune_s, 2),
+                       "autotune_best_ms": round(tune_ms, 4)},
+           "per_collection_launch": {"ms": round(coll_ms, 4), "distances_per_s": dists / (coll_ms * 1e-3),
+                                     "launches": len(batch)},
+           "one_query_per_launch": {"ms": round(query_ms, 4), "distances_per_s": dists / (query_ms * 1e-3),
+                                    "launches": sum(c["nq"] for c in batch)},
+           "sums_equal": bool(same),
+           "roofline": {"bound": "alu", "kernel": "batch_scan_kernel",
+                        "achieved": round(lookups / (batched_ms * 1e-3) / 1e12, 4),
+                        "peak": round(peak / 1e12, 4), "unit": "Tlookup/s",
+                        "frac": round(lookups / (batched_ms * 1e-3) / peak, 4), "peak_source": alu_peak.SOURCE,
+                        "sums_written_GB": round(sum(c["nq"] * c["n"] * 2 for c in batch) / 1e9, 3)},
+           "l2_cache": "every launch writes %.1f GB of sums (> L2)" % (sum(c["nq"] * c["n"] * 2 for c in batch) / 1e9)}
+    del plan, batch, plain
+    torch.cuda.empty_cache()
+    return res
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args, world, rank):
     """CPU oracle, bounded sample per step, on this host's cores."""
@@ -425,6 +544,7 @@ def run_bolt(args, world, rank, local):
         torch.cuda.empty_cache()
         line["large_n_scan"] = large_n_scan(C, quant, hbm_peak, peak_kind)
         line["encode_10m"] = encode_10m()
+        line["batched_collections"] = batched_collections()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
 
@@ -452,6 +572,7 @@ def roofline_topk(tk_ms, n, M, hbm_peak, peak_kind):
     return {"bound": "alu", "kernel": "topk_kernel", "achieved": round(achieved / 1e12, 4),
             "peak": round(peak_lookups / 1e12, 4), "unit": "Tlookup/s", "frac": round(achieved / peak_lookups, 4),
             "traffic": None, "peak_source": alu_peak.SOURCE,
+            "one_query_per_pass_cap": round(alu_peak.lookups_per_s_one_query() / 1e12, 4),
             "hbm_equivalent_GBps": round(n * M / 2 / (tk_ms * 1e-3) / 1e9, 1), "hbm_peak_GBps": hbm_peak,
             "hbm_peak_kind": peak_kind}
 
@@ -465,7 +586,13 @@ def run_only(args):
 
     torch.cuda.set_device(0)
     bolt.lib()
-    if args.only in ("encode10m", "encode10m_tc"):
+    if args.only == "batch":
+        batch = collections_setup(args.collections)
+        plan = bolt.BatchPlan([(c["codes"], c["n"], c["M"], c["luts"], c["sums"]) for c in batch])
+        plan.autotune()
+        print("tiles:", plan.tuning(), flush=True)
+        fn = lambda: plan.run()  # noqa: E731
+    elif args.only in ("encode10m", "encode10m_tc"):
         cfg = synth.CONFIGS["encode_10m"]
         n, J, M = 2_000_000, cfg["J"], cfg["M"]  # 2 GB of fp32 input: > L2, small for ncu
         X = synth.mixture_torch(n, J, seed=0)

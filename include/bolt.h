@@ -160,6 +160,70 @@ int bolt_topk_noalloc(const uint8_t *codes, int64_t n, int32_t M, const uint8_t 
                       int64_t nq, int32_t k, int32_t metric, uint16_t *out_sums,
                       int64_t *out_idx, void *stream);
 
+/* ---------------------------------------------------------------- batched scan
+ * The Sec. 3.1 scan of many independent collections -- each with its own
+ * encoded database, codebook count and query tables -- in ONE persistent
+ * launch.  (The paper scans one database at a time; batching collections is
+ * a serving form of the same sums.)  Results are exactly those of
+ * bolt_scan_l2 on each collection alone.
+ *
+ * One bolt_collection per collection; all pointers are device memory:
+ *   codes : blocked layout of n vectors and M codebooks (16-byte aligned)
+ *   luts  : nq x M x 16 uint8 tables (16-byte aligned)
+ *   sums  : nq rows of ld uint16, sums[q * ld + i] for i < n (16-byte
+ *           aligned; ld >= n and a multiple of 8).  Entries i in [n, ld) of
+ *           each row may be overwritten with padding sums.
+ *   n, nq : sizes (either may be 0: the collection then has no work)
+ *   M     : 1 <= M <= 256
+ *   qt_max: queries one warp accumulates in registers per pass over a code
+ *           block: 1, 2, 4, 8 or 16; 0 = library default (8)
+ *   units_per_warp: (block, query-tile) units each warp of a CTA takes per
+ *           task, 1..64; 0 = library default (4)
+ * qt_max and units_per_warp change speed only, never results;
+ * bolt_batch_autotune chooses them by timing. */
+typedef struct bolt_collection {
+    const uint8_t *codes;
+    const uint8_t *luts;
+    uint16_t *sums;
+    int64_t n;
+    int64_t nq;
+    int64_t ld;
+    int32_t M;
+    int32_t qt_max;
+    int32_t units_per_warp;
+    int32_t reserved; /* must be 0 */
+} bolt_collection;
+
+/* Bytes of device memory the plan for these collections needs (host only;
+ * < 0 with bolt_last_error set on invalid input). */
+int64_t bolt_batch_plan_bytes(const bolt_collection *colls_host, int32_t ncoll);
+
+/* Build the task list for colls_host[0..ncoll) on the host and copy it into
+ * `plan` (device, 256-byte aligned, plan_bytes >= bolt_batch_plan_bytes).
+ * Tasks are ordered largest collection first, and within a collection by
+ * code-block range, so that the query tiles of one range run close together
+ * and re-read its codes from L2.  Synchronizes `stream` (the copy comes from
+ * pageable host memory): build plans before any stream capture.  The plan
+ * holds the collections' pointers; it stays valid while they do. */
+int bolt_batch_plan(const bolt_collection *colls_host, int32_t ncoll, void *plan,
+                    int64_t plan_bytes, void *stream);
+
+/* Run a plan: one stream-ordered memset of its task counter and one
+ * persistent launch (one CTA per resident slot on every SM; CTAs take tasks
+ * from the counter).  Capturable in a CUDA graph.  Launches of one plan must
+ * not overlap on the GPU (they share the counter). */
+int bolt_scan_batched(const void *plan, void *stream);
+
+/* Choose qt_max and units_per_warp for every collection by timing
+ * bolt_scan_batched on the collections themselves, one codebook count M at
+ * a time, over the candidates qt_max in {4, 8, 16} (capped by the table
+ * space) x units_per_warp in {1, 2, 4, 8}; writes the fastest into
+ * colls_host.  Overwrites the collections' sums; allocates and frees a
+ * scratch plan and synchronizes `stream`.  tuning_ms_host (nullable)
+ * receives the best time of the whole batch with the chosen settings. */
+int bolt_batch_autotune(bolt_collection *colls_host, int32_t ncoll, void *stream,
+                        float *tuning_ms_host);
+
 /* ---------------------------------------------------------------- dequantize
  * Sec. 3.2: the per-table reconstructions beta_m/a + b_m sum to
  * S * (1/a) + sum_m b_m.  Host helper (fp64, no GPU): inv_a =

@@ -55,7 +55,19 @@ _SIGS = {
                             C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_fit_quantizer": ([C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_batch_plan_bytes": ([C.c_void_p, C.c_int32], C.c_int64),
+    "bolt_batch_plan": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
+    "bolt_scan_batched": ([C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_batch_autotune": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
 }
+
+
+class Collection(C.Structure):
+    """struct bolt_collection (include/bolt.h)."""
+
+    _fields_ = [("codes", C.c_void_p), ("luts", C.c_void_p), ("sums", C.c_void_p), ("n", C.c_int64),
+                ("nq", C.c_int64), ("ld", C.c_int64), ("M", C.c_int32), ("qt_max", C.c_int32),
+                ("units_per_warp", C.c_int32), ("reserved", C.c_int32)]
 
 
 def lib():
@@ -286,3 +298,61 @@ def fit_quantizer(Qtrain, centroids, metric, stream=None):
     _check(lib().bolt_fit_quantizer(_ptr(Qtrain), nqt, J, M, _ptr(centroids), metric, C.byref(a),
                                     b.ctypes.data_as(C.c_void_p), C.byref(ai), _stream(stream)))
     return np.float32(a.value), b, int(ai.value)
+
+
+# ------------------------------------------------------------------ batched scan
+def sums_ld(n):
+    """Row stride (uint16 entries) of a batched-scan sums matrix: n rounded up to 8."""
+    return (n + 7) // 8 * 8
+
+
+class BatchPlan:
+    """A device-resident task list over many collections (bolt_batch_plan).
+
+    ``entries`` is a list of (codes, n, M, luts, sums) with torch CUDA
+    tensors: codes blocked, luts (nq, M, 16) uint8, sums (nq, sums_ld(n))
+    uint16.  The plan keeps references to the tensors so their memory stays
+    alive while the plan exists.
+    """
+
+    def __init__(self, entries, tuning=None, stream=None):
+        torch = _torch()
+        self._keep = []
+        arr = (Collection * max(1, len(entries)))()
+        for i, (codes, n, M, luts, sums) in enumerate(entries):
+            _dev(codes, torch.uint8, "codes")
+            _dev(luts, torch.uint8, "luts")
+            _dev(sums, torch.uint16, "sums")
+            nq = luts.shape[0]
+            ld = sums.shape[1] if sums.dim() == 2 else sums_ld(n)
+            arr[i] = Collection(codes.data_ptr(), luts.data_ptr(), sums.data_ptr(), n, nq, ld, M, 0, 0, 0)
+            if tuning is not None:
+                arr[i].qt_max, arr[i].units_per_warp = tuning[i]
+            self._keep += [codes, luts, sums]
+        self.ncoll = len(entries)
+        self.colls = arr
+        self.device = entries[0][0].device if entries else torch.device("cuda")
+        self._upload(stream)
+
+    def tuning(self):
+        return [(self.colls[i].qt_max, self.colls[i].units_per_warp) for i in range(self.ncoll)]
+
+    def _upload(self, stream):
+        torch = _torch()
+        nbytes = int(lib().bolt_batch_plan_bytes(C.cast(self.colls, C.c_void_p), self.ncoll))
+        if nbytes < 0:
+            raise BoltError(-nbytes, lib().bolt_last_error().decode())
+        self.plan = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        _check(lib().bolt_batch_plan(C.cast(self.colls, C.c_void_p), self.ncoll, _ptr(self.plan), self.plan.numel(),
+                                     _stream(stream)))
+
+    def autotune(self, stream=None):
+        """Time the candidates (bolt_batch_autotune), keep the fastest, re-plan.
+        Returns the batch time (ms) with the chosen settings."""
+        ms = C.c_float(0.0)
+        _check(lib().bolt_batch_autotune(C.cast(self.colls, C.c_void_p), self.ncoll, _stream(stream), C.byref(ms)))
+        self._upload(stream)
+        return ms.value
+
+    def run(self, stream=None):
+        _check(lib().bolt_scan_batched(_ptr(self.plan), _stream(stream)))

@@ -79,3 +79,42 @@ def test_binding_fails_loudly_without_cuda():
         pytest.skip("a GPU is present")
     with pytest.raises(bolt.BoltError):
         bolt.encode(torch.zeros(4, 8), torch.zeros(2, 16, 4))
+
+
+def _coll(n, M, nq, ld=None, qt=0, upw=0, codes=0x10000, luts=0x20000, sums=0x30000, reserved=0):
+    return bolt.Collection(codes, luts, sums, n, nq, bolt.sums_ld(n) if ld is None else ld, M, qt, upw, reserved)
+
+
+def _plan_bytes(*colls):
+    arr = (bolt.Collection * max(1, len(colls)))(*colls)
+    return int(bolt.lib().bolt_batch_plan_bytes(C.cast(arr, C.c_void_p), len(colls)))
+
+
+def test_batch_planner_task_counts():
+    """Host planner: 64-byte header, a 48-byte record per collection and a
+    24-byte task per (query group, block range)."""
+    H, R, T = 64, 48, 24
+    assert _plan_bytes() == H
+    # 64 blocks, 16 queries, qt 8: one group of 2 tiles; 8 warps x 4 units
+    # per task = 32 units = 16 blocks x 2 tiles -> 4 tasks
+    assert _plan_bytes(_coll(64 * 256, 16, 16, qt=8, upw=4)) == H + R + 4 * T
+    # 37 queries at qt 8: tiles 8,8,8,8 (one group) + 4 + 1; 1 block each
+    assert _plan_bytes(_coll(100, 16, 37, qt=8, upw=4)) == H + R + 3 * T
+    # M = 256: 16 x 256 table rows exceed the 1024 staged, so qt drops to 4
+    # and a group holds one tile: 9 queries -> tiles 4, 4, 1 -> 3 groups
+    assert _plan_bytes(_coll(256, 256, 9, qt=16, upw=1)) == H + R + 3 * T
+    # empty collections have no tasks but keep their record
+    assert _plan_bytes(_coll(0, 8, 5), _coll(100, 8, 0)) == H + 2 * R
+
+
+def test_batch_planner_rejects_bad_collections():
+    L = bolt.lib()
+    bad = [_coll(100, 0, 2), _coll(100, 257, 2), _coll(100, 8, 2, ld=100), _coll(100, 8, 2, ld=96),
+           _coll(100, 8, 2, qt=3), _coll(100, 8, 2, upw=65), _coll(100, 8, 2, reserved=1),
+           _coll(100, 8, 2, codes=0x10001), _coll(100, 8, 2, sums=0), _coll(-1, 8, 2)]
+    for c in bad:
+        assert _plan_bytes(c) < 0
+        assert L.bolt_last_error()
+    # a bad record anywhere fails the whole batch
+    assert _plan_bytes(_coll(100, 8, 2), _coll(100, 8, 2, qt=5)) < 0
+    assert L.bolt_scan_batched(C.c_void_p(0), C.c_void_p(0)) == bolt.EINVAL
