@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--nq", type=int, default=None, help="override query count (profiling runs)")
     ap.add_argument("--no-aux", action="store_true", help="skip the large-N and encode side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["topk1m", "topk50m", "encode10m", "encode10m_tc", "batch"], default=None,
+    ap.add_argument("--only", choices=["topk1m", "topk50m", "encode10m", "encode10m_tc", "batch", "serve"], default=None,
                     help="profiling run: set up one workload and launch only its kernel a few times")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--graph-reps", type=int, default=0, help="also time graph replays of the launches")
@@ -217,7 +217,30 @@ def prepare(cfg, data_seed, device="cuda"):
     return X, Q, Xd, Qd, C, quant
 
 
-def large_n_scan(C, quant, hbm_peak, peak_kind):
+def build_50m(C):
+    """Codes of the 50,000,000 x 128 mixture database (M = 16), encoded in
+    2M-row chunks generated on the device."""
+    import torch
+
+    from paper_1706_10283_gb300 import bolt, synth
+
+    cfg = synth.CONFIGS["serve_50m"]
+    n, J, M = cfg["n"], cfg["J"], cfg["M"]
+    codes = torch.empty(bolt.codes_bytes(n, M), dtype=torch.uint8, device="cuda")
+    chunk = 1 << 21  # 2,097,152 rows (multiple of 256)
+    buf = torch.empty((chunk, J), dtype=torch.float32, device="cuda")
+    for lo in range(0, n, chunk):
+        hi = min(n, lo + chunk)
+        X = synth.mixture_torch(hi - lo, J, seed=5000 + lo // chunk, out=buf[:hi - lo])
+        row0 = lo // 256 * M * 128
+        bolt.encode(X, C, out=codes[row0:row0 + bolt.codes_bytes(hi - lo, M)])
+    del buf
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return codes
+
+
+def large_n_scan(codes, C, quant, hbm_peak, peak_kind):
     """One L2 top-100 query per launch over 50,000,000 encoded vectors."""
     import torch
 
@@ -225,16 +248,6 @@ def large_n_scan(C, quant, hbm_peak, peak_kind):
 
     cfg = synth.CONFIGS["serve_50m"]
     n, J, M, k = cfg["n"], cfg["J"], cfg["M"], 100
-    codes = torch.empty(bolt.codes_bytes(n, M), dtype=torch.uint8, device="cuda")
-    chunk = 1 << 21  # 2,097,152 rows (multiple of 256)
-    buf = torch.empty((chunk, J), dtype=torch.float32, device="cuda")
-    g = torch.Generator(device="cuda")
-    for lo in range(0, n, chunk):
-        hi = min(n, lo + chunk)
-        X = synth.mixture_torch(hi - lo, J, seed=5000 + lo // chunk, out=buf[:hi - lo])
-        row0 = lo // 256 * M * 128
-        bolt.encode(X, C, out=codes[row0:row0 + bolt.codes_bytes(hi - lo, M)])
-    del buf, g
     Q = torch.from_numpy(synth.mixture(8, J, 77)).cuda()
     a, b = quant[bolt.METRIC_L2]
     luts = bolt.build_luts(Q, C, bolt.METRIC_L2, a, b)
@@ -254,14 +267,66 @@ def large_n_scan(C, quant, hbm_peak, peak_kind):
     ms = ev[0].elapsed_time(ev[1]) / reps
     code_bytes = n * M / 2
     gbs = code_bytes / (ms * 1e-3) / 1e9
-    del codes
-    torch.cuda.empty_cache()
+    del ws
     return {"workload": "serve_50m: 50,000,000 x 128 mixture, M=16 (400 MB codes > L2), L2 top-100, "
                         "1 query per launch, inputs larger than L2",
             "kernel": "topk_kernel", "ms_per_launch": round(ms, 4),
             "distances_per_s": n / (ms * 1e-3), "code_GBps": round(gbs, 1), "hbm_peak_GBps": hbm_peak,
             "peak": peak_kind, "frac_of_hbm": round(gbs / hbm_peak, 4),
             "algorithmic_bytes_per_launch": code_bytes}
+
+
+def serving(codes50, C, quant, count=300, rate=40.0, slots=4, budget_gb=16.0):
+    """Serving trace on the resident 50M-vector database plus the encoded
+    100,000 x 512 matmul operand (M = 32): Poisson arrivals, 1..512 queries
+    per request, L2 / dot, k 10..100, 10% approximate-matmul requests
+    (1..512 rows of A); the continuous-batching server against the plain
+    one-query-per-launch form on the same trace."""
+    import torch
+
+    from paper_1706_10283_gb300 import bolt, serve, synth
+
+    cfg = synth.CONFIGS["serve_50m"]
+    mm = synth.CONFIGS["matmul_4096x512_100k"]
+    B = synth.mixture_torch(mm["n"], mm["J"], seed=900)
+    CB, aB, bB = bolt.fit_codebooks(B[:50_000].contiguous(), mm["M"], 8, synth.kmeans_init_rows(50_000, 900),
+                                    Qtrain=B[torch.from_numpy(synth.train_query_rows(mm["n"], 900)).cuda()]
+                                    .contiguous(), metric=bolt.METRIC_DOT)
+    codesB = bolt.encode(B, CB)
+    del B
+    trace = synth.poisson_trace(11, count, rate, cfg["J"], matmul_frac=0.1, J_mm=mm["J"])
+
+    def requests():
+        return [serve.Request(i, "B" if r["kind"] == "matmul" else "db", r["Q"], kind=r["kind"],
+                              metric=r["metric"], k=r["k"], t_arrival=r["t_arrival"]) for i, r in enumerate(trace)]
+
+    srv = serve.Server(int(budget_gb * 2**30), slots=slots)
+    srv.add_collection("db", codes50, cfg["n"], cfg["M"], C, quant)
+    srv.add_collection("B", codesB, mm["n"], mm["M"], CB, {bolt.METRIC_DOT: (aB, bB), bolt.METRIC_L2: (aB, bB)})
+    n_of = {"db": cfg["n"], "B": mm["n"]}
+    # warm-up: a few requests through both forms (kernel attributes, pinned buffers)
+    warm = requests()[:6]
+    for r in warm:
+        r.t_arrival = 0.0
+    serve.run_trace(srv, warm)
+    serve.run_plain(srv.collections, requests()[:2])
+    torch.cuda.synchronize()
+    got = serve.run_trace(srv, requests())
+    srv_stats = serve.latency_stats(got, n_of)
+    srv_stats.update(batches=srv.batches, launches=srv.launches, slots=slots,
+                     budget_bytes=srv.budget.total, peak_budget_bytes=srv.budget.peak)
+    plain = serve.run_plain(srv.collections, requests())
+    plain_stats = serve.latency_stats(plain, n_of)
+    by = {r.rid: r for r in plain}
+    same = all((np.array_equal(r.out, by[r.rid].out) if r.kind == "matmul" else
+                (np.array_equal(r.idx, by[r.rid].idx) and np.array_equal(r.dist, by[r.rid].dist))) for r in got)
+    del srv, codesB
+    torch.cuda.empty_cache()
+    return {"workload": "serve_50m: resident 50,000,000 x 128 (M=16, 400 MB codes) + matmul B 100,000 x 512 "
+                        "(M=32); %d Poisson requests at %.0f/s, 1-512 queries (log-uniform), L2/dot, k 10-100, "
+                        "10%% matmul (1-512 rows of A)" % (count, rate),
+            "server": srv_stats, "plain_one_query_per_launch": plain_stats, "results_identical": bool(same),
+            "latency": "host time from scheduled arrival to results in host memory"}
 
 
 def encode_10m():
@@ -542,7 +607,11 @@ def run_bolt(args, world, rank, local):
     if rank == 0 and not args.no_aux:
         del step
         torch.cuda.empty_cache()
-        line["large_n_scan"] = large_n_scan(C, quant, hbm_peak, peak_kind)
+        codes50 = build_50m(C)
+        line["large_n_scan"] = large_n_scan(codes50, C, quant, hbm_peak, peak_kind)
+        line["serving"] = serving(codes50, C, quant)
+        del codes50
+        torch.cuda.empty_cache()
         line["encode_10m"] = encode_10m()
         line["batched_collections"] = batched_collections()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -586,6 +655,13 @@ def run_only(args):
 
     torch.cuda.set_device(0)
     bolt.lib()
+    if args.only == "serve":
+        cfg = workload(8)
+        X, Q, Xd, Qd, C, quant = prepare(cfg, 0)
+        del X, Xd
+        codes50 = build_50m(C)
+        print(json.dumps(serving(codes50, C, quant)), flush=True)
+        return
     if args.only == "batch":
         batch = collections_setup(args.collections)
         plan = bolt.BatchPlan([(c["codes"], c["n"], c["M"], c["luts"], c["sums"]) for c in batch])

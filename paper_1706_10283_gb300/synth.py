@@ -30,6 +30,11 @@ Recipes
   ``default_rng(seed + 1).choice(n, count, replace=False)``.
 * ``collections(seed=3, count=64)``: the multi-collection batch: N log-uniform
   in [1e3, 2e6], J in {64, 128, 256}, M in {8, 16, 32}, 1..256 queries each.
+* ``poisson_trace(seed, count, rate, ...)``: a serving trace: exponential
+  inter-arrival times of mean 1/rate seconds, request sizes log-uniform in
+  [1, max_q] queries (rounded down), metric L2 or dot with probability 1/2,
+  k uniform in [k_lo, k_hi], a fraction ``matmul_frac`` of approximate-matmul
+  requests; each request's queries are ``mixture(nq, J, 10_000 + i)`` rows.
 """
 import math
 
@@ -110,6 +115,25 @@ def collections(seed=3, count=64, n_lo=1e3, n_hi=2e6):
         M = int(rng.choice([8, 16, 32]))
         nq = int(rng.integers(1, 257))
         out.append(dict(n=n, J=J, M=M, nq=nq, data_seed=1000 + i, query_seed=2000 + i))
+    return out
+
+
+def poisson_trace(seed, count, rate, J, max_q=512, k_lo=10, k_hi=100, matmul_frac=0.0, J_mm=None, max_rows=512):
+    """List of dicts {t_arrival, kind, nq, metric, k, Q} (t in seconds from 0)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        mm = matmul_frac > 0 and rng.uniform() < matmul_frac
+        top = max_rows if mm else max_q
+        nq = int(math.floor(2 ** rng.uniform(0, math.log2(top + 1))))
+        nq = max(1, min(top, nq))
+        metric = int(rng.integers(0, 2))
+        k = int(rng.integers(k_lo, k_hi + 1))
+        d = J_mm if mm else J
+        out.append(dict(t_arrival=t, kind="matmul" if mm else "search", nq=nq, metric=metric, k=k,
+                        Q=mixture(nq, d, 10_000 + i)))
     return out
 
 
