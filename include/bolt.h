@@ -224,6 +224,22 @@ int bolt_scan_batched(const void *plan, void *stream);
 int bolt_batch_autotune(bolt_collection *colls_host, int32_t ncoll, void *stream,
                         float *tuning_ms_host);
 
+/* ---------------------------------------------------------------- shard merge
+ * Top-k of a database split into disjoint row ranges (shards): every
+ * distance depends on one vector's codes only (Sec. 3.1), so the global
+ * top-k is the best k of the union of the shards' own top-k lists.
+ * sums, idx: nshard x nq x k, shard-major; list (a, q) is bolt_topk's output
+ * for query q on shard a (best first, local indices, padding index -1;
+ * index -2 marks a failed wait and makes the merged row -2).
+ * offsets: nshard int64 (device), global index of each shard's row 0.
+ * out_sums / out_idx: nq x k, the same order and padding as bolt_topk over
+ * the whole database, so the merge is bit-identical to the unsharded
+ * result.  All pointers are device memory.  M and metric as in bolt_topk
+ * (dot lists are merged by largest sum). */
+int bolt_topk_merge(const uint16_t *sums, const int64_t *idx, const int64_t *offsets,
+                    int32_t nshard, int64_t nq, int32_t k, int32_t M, int32_t metric,
+                    uint16_t *out_sums, int64_t *out_idx, void *stream);
+
 /* ---------------------------------------------------------------- dequantize
  * Sec. 3.2: the per-table reconstructions beta_m/a + b_m sum to
  * S * (1/a) + sum_m b_m.  Host helper (fp64, no GPU): inv_a =

@@ -55,6 +55,8 @@ _SIGS = {
                             C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_fit_quantizer": ([C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_topk_merge": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.c_int32,
+                         C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_batch_plan_bytes": ([C.c_void_p, C.c_int32], C.c_int64),
     "bolt_batch_plan": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "bolt_scan_batched": ([C.c_void_p, C.c_void_p], C.c_int),
@@ -228,6 +230,24 @@ def topk(codes, n, M, luts, k, metric, out_sums=None, out_idx=None, workspace=No
     wbytes = workspace.numel() if workspace is not None else 0
     _check(lib().bolt_topk(_ptr(codes), n, M, _ptr(luts), nq, k, metric, _ptr(out_sums), _ptr(out_idx),
                            _ptr(workspace), wbytes, _stream(stream)))
+    return out_sums, out_idx
+
+
+def topk_merge(sums, idx, offsets, M, metric, out_sums=None, out_idx=None, stream=None):
+    """Merge per-shard top-k lists: sums (nshard, nq, k) uint16, idx (nshard,
+    nq, k) int64 local indices, offsets (nshard,) int64 device tensor of
+    global row offsets.  Returns (sums, idx) of shape (nq, k)."""
+    torch = _torch()
+    _dev(sums, torch.uint16, "sums")
+    _dev(idx, torch.int64, "idx")
+    _dev(offsets, torch.int64, "offsets")
+    nshard, nq, k = idx.shape
+    if out_sums is None:
+        out_sums = torch.empty((nq, k), dtype=torch.uint16, device=idx.device)
+    if out_idx is None:
+        out_idx = torch.empty((nq, k), dtype=torch.int64, device=idx.device)
+    _check(lib().bolt_topk_merge(_ptr(sums), _ptr(idx), _ptr(offsets), nshard, nq, k, M, metric, _ptr(out_sums),
+                                 _ptr(out_idx), _stream(stream)))
     return out_sums, out_idx
 
 
