@@ -728,6 +728,9 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int plan_topk(int64_t n, int32_t M, int32_t k, TopkPlan *plan) {
     BOLT_REQUIRE(k >= 1 && k <= kMaxK, BOLT_EUNSUPPORTED, "k=%d outside [1, %d]", k, kMaxK);
+    plan->small = 0;
+    plan->nbc = 0;
+    if (plan_topk_small(n, M, k, device_sm_count(), plan)) return BOLT_OK;
     // Two blocks per unit of work for small M on large databases (amortizes
     // per-unit overhead once every warp has many blocks to stream).
     const int64_t blocks_per_warp = num_blocks(n) / ((int64_t)(device_sm_count() > 0 ? device_sm_count() : 1) * 16);
@@ -773,7 +776,7 @@ int plan_topk(int64_t n, int32_t M, int32_t k, TopkPlan *plan) {
 size_t topk_header_bytes(int64_t nq) { return align_up((size_t)nq * 12, 256) + (size_t)nq * kBins * 4; }
 
 int64_t topk_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k) {
-    (void)k;
+    if (plan.small) return topk_small_workspace_bytes(plan, nq, k);
     return (int64_t)(topk_header_bytes(nq) + (size_t)nq * plan.list_cap * 8);
 }
 
@@ -809,6 +812,8 @@ static int launch_w(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *l
 int launch_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, int32_t k,
                 int32_t metric, uint16_t *out_sums, int64_t *out_idx, void *workspace, const TopkPlan &plan,
                 cudaStream_t stream) {
+    if (plan.small) return launch_topk_small(codes, n, M, luts, nq, k, metric, out_sums, out_idx, workspace, plan,
+                                             stream);
     BOLT_REQUIRE(nq <= 65535, BOLT_EUNSUPPORTED, "nq=%lld > 65535 per call", (long long)nq);
     BOLT_CUDA(cudaMemsetAsync(workspace, 0, topk_header_bytes(nq), stream));
     const TopkWS w = carve_topk_ws(workspace, plan, nq, k);

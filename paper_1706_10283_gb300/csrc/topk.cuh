@@ -6,18 +6,26 @@
 namespace bolt {
 
 constexpr int kBins = 4096;  // histogram bins over candidate sums
+// Shared-memory size class (topk_small.cu): every CTA's codes and sums fit in
+// shared memory and the last CTA merges at most kSmallMergeKeys keys.
+constexpr int kSmallMergeKeys = 16384;
+constexpr int kMaxSmallK = 1024;
+constexpr size_t kSmallMaxSmem = 220 * 1024;
 
 struct TopkPlan {
+    int small;            // 1: shared-memory size class (topk_small.cu); the fields below
+                          //    marked (s) are the ones it uses
+    int nbc;              // (s) code blocks per CTA
     int warps;            // warps per CTA (16, 8, 4 or 2, by stage size)
     int bpi;              // code blocks per unit of work (one bulk copy)
     int stages;           // TMA stages per warp
-    int grid;             // CTAs per query
+    int grid;             // (s) CTAs per query
     int cap;              // candidate-buffer entries per CTA
-    int hshift;           // histogram bin width 2^hshift
+    int hshift;           // (s) histogram bin width 2^hshift
     int out_cap;          // candidates one CTA may append (k <= out_cap <= 2k)
     int list_cap;         // per-query candidate list capacity (grid * out_cap)
     int64_t blocks_per_cta;  // units of work per CTA
-    size_t smem_bytes;
+    size_t smem_bytes;    // (s)
 };
 
 // Per-query device state in the workspace.
@@ -33,6 +41,12 @@ int plan_topk(int64_t n, int32_t M, int32_t k, TopkPlan *plan);
 int64_t topk_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k);
 TopkWS carve_topk_ws(void *ws, const TopkPlan &plan, int64_t nq, int32_t k);
 size_t topk_header_bytes(int64_t nq);  // fill/ticket/status + histograms (zeroed per call)
+
+bool plan_topk_small(int64_t n, int32_t M, int32_t k, int sms, TopkPlan *plan);
+int64_t topk_small_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k);
+int launch_topk_small(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, int32_t k,
+                      int32_t metric, uint16_t *out_sums, int64_t *out_idx, void *workspace, const TopkPlan &plan,
+                      cudaStream_t stream);
 
 int launch_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, int32_t k,
                 int32_t metric, uint16_t *out_sums, int64_t *out_idx, void *workspace, const TopkPlan &plan,

@@ -1,0 +1,518 @@
+// Fused scan + exact top-k for databases whose codes fit, spread over one
+// wave of CTAs, in shared memory (about 2.5M vectors at M = 16).
+//
+// Latency, not bandwidth, decides this size class: every CTA holds only a
+// few dozen 256-vector blocks, so the kernel avoids every cooperative phase
+// and global round trip of the streaming kernel.
+//
+// Per CTA (one contiguous range of blocks):
+//   1. one thread starts 1-D bulk copies of the whole code range into shared
+//      memory (chunks of 8 blocks, one mbarrier each) while the others load
+//      the query table;
+//   2. each warp scans blocks as their chunk lands, writes the 8 sums of each
+//      lane as keys s' (s' = S for L2, 255*M - S for dot; 0xFFFF for padding
+//      vectors) to a shared array in vector order, and counts them in a
+//      4,096-bin histogram of s' >> hshift;
+//   3. the exact k-th smallest s' (T) and the number below it (c_lt) come
+//      from the histogram (plus a second count inside T's bin when bins are
+//      wider than 1); the CTA adds the per-bin counts of the keys it keeps to
+//      the query's global histogram (one atomic per non-empty bin);
+//   4. an ordered compaction keeps every s' < T and the first k - c_lt
+//      entries with s' == T, in vector order: that is the CTA's exact top-k
+//      with ties to the lower index; it is published to the CTA's slot of a
+//      global list, sorted by (s', index).
+// The last CTA to finish (atomic ticket) reads the global histogram, which
+// gives the k-th smallest s' of the union of the lists and the number of
+// keys below it; every list then contributes a prefix (binary search), the
+// ties at the threshold taken in vector order (CTA ranges are ordered), and
+// the k survivors are sorted and written.
+#include "topk.cuh"
+
+#include "scan_core.cuh"
+
+namespace bolt {
+
+constexpr int kSmallThreads = 512;
+constexpr int kSmallWarps = kSmallThreads / 32;
+constexpr int kSmallChunk = 8;  // blocks per bulk copy
+constexpr uint64_t kSmallWait = 1000000000ull;  // 1 s bound on every mbarrier wait
+constexpr int kSmallMiscWords = 64;
+constexpr uint32_t kPad = 0xFFFFu;  // s' of padding vectors (every real s' <= 255 * 256)
+
+// Exclusive block-wide prefix sum of one value per thread (T = 512).
+// wsum: kSmallWarps + 1 words of shared scratch.  Returns the prefix and the
+// total; ends with a barrier so wsum may be reused at once.
+__device__ __forceinline__ uint32_t small_scan(uint32_t v, uint32_t *wsum, uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t x = lane < kSmallWarps ? wsum[lane] : 0u;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, x, off);
+            if (lane >= off) x += t;
+        }
+        if (lane < kSmallWarps) wsum[lane] = x;  // inclusive warp totals
+    }
+    __syncthreads();
+    const uint32_t before = warp > 0 ? wsum[warp - 1] : 0u;
+    total = wsum[kSmallWarps - 1];
+    __syncthreads();
+    return before + incl - v;
+}
+
+// Smallest bin b of hist[0..kBins) with (#entries in bins < b) < kk <= (#in
+// bins <= b); returns b and sets below = #entries in bins < b.  kk >= 1 and
+// kk <= total are required.
+__device__ __forceinline__ uint32_t small_find(const uint32_t *hist, uint32_t kk, uint32_t *misc, uint32_t *wsum,
+                                               uint32_t &below) {
+    constexpr int BPT = kBins / kSmallThreads;  // 8
+    const int tid = threadIdx.x;
+    uint32_t v[BPT], local = 0;
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        v[i] = hist[tid * BPT + i];
+        local += v[i];
+    }
+    uint32_t total;
+    const uint32_t excl = small_scan(local, wsum, total);
+    if (excl < kk && kk <= excl + local) {
+        uint32_t c = excl;
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            if (c < kk && kk <= c + v[i]) {
+                misc[0] = (uint32_t)(tid * BPT + i);
+                misc[1] = c;
+            }
+            c += v[i];
+        }
+    }
+    __syncthreads();
+    below = misc[1];
+    const uint32_t b = misc[0];
+    __syncthreads();
+    return b;
+}
+
+// Ordered compaction: entry e (vector order) is kept if s' < T, or s' == T
+// and fewer than r entries with s' == T precede it; emit(pos, e) receives its
+// rank among the kept entries (so kept entries stay in vector order).
+template <typename F, typename E>
+__device__ __forceinline__ void small_keep(int L, uint32_t T, uint32_t r, F s, E emit, uint32_t *wsum) {
+    const int tid = threadIdx.x;
+    const int seg = (L + kSmallThreads - 1) / kSmallThreads;
+    const int e0 = min(L, tid * seg), e1 = min(L, e0 + seg);
+    uint32_t lt = 0, eq = 0;
+    for (int e = e0; e < e1; ++e) {
+        const uint32_t v = s(e);
+        lt += v < T ? 1u : 0u;
+        eq += v == T ? 1u : 0u;
+    }
+    uint32_t tl, te;
+    uint32_t lt_before = small_scan(lt, wsum, tl);
+    uint32_t eq_before = small_scan(eq, wsum, te);
+    for (int e = e0; e < e1; ++e) {
+        const uint32_t v = s(e);
+        if (v < T) {
+            emit(lt_before + min(eq_before, r), e);
+            ++lt_before;
+        } else if (v == T) {
+            if (eq_before < r) emit(lt_before + eq_before, e);
+            ++eq_before;
+        }
+    }
+    __syncthreads();
+}
+
+__host__ __device__ constexpr size_t small_align_dev(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct SmallWS {
+    uint32_t *ticket;  // [nq]
+    uint32_t *status;  // [nq] bit 0: a bounded wait gave up
+    uint32_t *ghist;   // [nq][kBins] histogram of s' >> hshift over every CTA's kept keys
+    uint32_t *cnt;     // [nq][G] entries in each CTA's list
+    uint64_t *keys;    // [nq][G * k rounded up to even] (s' << 32 | index), vector order within a list
+};
+
+template <int MT>
+__global__ void __launch_bounds__(kSmallThreads, 1)
+    topk_small_kernel(const uint32_t *__restrict__ codes, int64_t n, int32_t M, const uint8_t *__restrict__ luts,
+                      int32_t k, int32_t metric, SmallWS ws, int nbc, int hshift,
+                      uint16_t *__restrict__ out_sums, int64_t *__restrict__ out_idx) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    if (MT > 0) M = MT;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t q = blockIdx.y;
+    const int G = gridDim.x, cta = blockIdx.x;
+
+    uint8_t *p = smem;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(p);
+    p += kBins * 4;
+    uint32_t *misc = reinterpret_cast<uint32_t *>(p);  // [0..2) find results, [2] failed, [3] last, [8..) scan
+    uint32_t *wsum = misc + 8;
+    p += kSmallMiscWords * 4;
+    uint4 *lut = reinterpret_cast<uint4 *>(p);
+    p += (size_t)M * 16;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(p);
+    const int nch = (nbc + kSmallChunk - 1) / kSmallChunk;
+    p += (size_t)((nch + 2) / 2 * 2) * 8;  // one barrier per chunk + the merge copy's
+    uint8_t *region = p;  // codes + sums during the scan; keys during the merge
+    const uint32_t blk_bytes = (uint32_t)M * kRowBytes;
+    uint32_t *codes_s = reinterpret_cast<uint32_t *>(region);
+    uint16_t *sums_s = reinterpret_cast<uint16_t *>(region + (size_t)nbc * blk_bytes);
+
+    const int64_t nb = num_blocks(n);
+    const int64_t b0 = (int64_t)cta * nbc;
+    const int nblk = (int)min((int64_t)nbc, nb - b0);  // >= 1 (grid = ceil(nb / nbc))
+    const int nchunks = (nblk + kSmallChunk - 1) / kSmallChunk;
+
+    if (tid == 0) {
+        for (int c = 0; c < nchunks; ++c) mbar_init(&bars[c], 1);
+        fence_mbar_init();
+        misc[2] = 0;
+        for (int c = 0; c < nchunks; ++c) {
+            const int nbk = min(kSmallChunk, nblk - c * kSmallChunk);
+            const uint32_t bytes = (uint32_t)nbk * blk_bytes;
+            mbar_arrive_expect_tx(&bars[c], bytes);
+            bulk_g2s(region + (size_t)c * kSmallChunk * blk_bytes,
+                     codes + (size_t)(b0 + (int64_t)c * kSmallChunk) * M * kRowWords, bytes, &bars[c]);
+        }
+    }
+    for (int i = tid; i < kBins; i += kSmallThreads) hist[i] = 0;
+    const uint4 *lut_g = reinterpret_cast<const uint4 *>(luts + q * M * kK);
+    for (int i = tid; i < M; i += kSmallThreads) lut[i] = lut_g[i];
+    __syncthreads();
+
+    const uint32_t smax = 255u * (uint32_t)M;
+    bool failed = false;
+    for (int blk = warp; blk < nblk; blk += kSmallWarps) {
+        // (a completed chunk's barrier answers at once)
+        const bool ok = mbar_wait_bounded(&bars[blk / kSmallChunk], 0u, kSmallWait);
+        if (!__all_sync(0xFFFFFFFFu, ok)) {
+            failed = true;
+            break;
+        }
+        const uint32_t *words = codes_s + (size_t)blk * M * kRowWords;
+        Acc8 acc;
+        acc.zero();
+        if (MT > 0) {
+#pragma unroll
+            for (int m = 0; m < MT; ++m) acc.add(prep_word(words[m * kRowWords + lane]), lut[m]);
+        } else {
+#pragma unroll 4
+            for (int m = 0; m < M; ++m) acc.add(prep_word(words[m * kRowWords + lane]), lut[m]);
+        }
+        uint32_t e_lo, o_lo, e_hi, o_hi;
+        acc.finish(e_lo, o_lo, e_hi, o_hi);
+        const uint4 pk = pack_sums(e_lo, o_lo, e_hi, o_hi);
+        const uint32_t w[4] = {pk.x, pk.y, pk.z, pk.w};
+        const int64_t v0 = (b0 + blk) * kBlockVecs + 8 * lane;
+        uint32_t out[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            uint32_t pair = 0;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int i = 2 * h + j;
+                const uint32_t S = (w[h] >> (16 * j)) & 0xFFFFu;
+                uint32_t sp = metric == BOLT_METRIC_DOT ? smax - S : S;
+                if (v0 + i >= n) sp = kPad;
+                else atomicAdd(&hist[sp >> hshift], 1u);
+                pair |= sp << (16 * j);
+            }
+            out[h] = pair;
+        }
+        *reinterpret_cast<uint4 *>(sums_s + (size_t)blk * kBlockVecs + 8 * lane) =
+            make_uint4(out[0], out[1], out[2], out[3]);
+    }
+    if (failed && lane == 0) atomicOr(&misc[2], 1u);
+    __syncthreads();
+    const bool bad = misc[2] != 0u;
+    if (bad) {
+        // let copies still in flight land before shared memory is reused
+        if (tid == 0)
+            for (int c = 0; c < nchunks; ++c) mbar_wait_bounded(&bars[c], 0u, kSmallWait / 10);
+        __syncthreads();
+    }
+
+    // ---- this CTA's exact top-k, published sorted by (s', index)
+    const int L = nblk * kBlockVecs;
+    const int64_t nvalid = min((int64_t)L, n - b0 * kBlockVecs);
+    const uint32_t kk = (uint32_t)min((int64_t)k, nvalid);
+    auto s_of = [&](int e) -> uint32_t { return sums_s[e]; };
+    const int64_t qstride = ((int64_t)G * k + 1) & ~(int64_t)1;  // even: 16-byte aligned per query
+    uint64_t *mine = ws.keys + q * qstride + (int64_t)cta * k;
+    uint64_t *kept = reinterpret_cast<uint64_t *>(
+        region + small_align_dev((size_t)nbc * blk_bytes + (size_t)nbc * kBlockVecs * 2, 16));
+    if (!bad) {
+        uint32_t below;
+        const uint32_t B = small_find(hist, kk, misc, wsum, below);
+        // The query's global histogram counts every CTA's kept keys: all of
+        // bins < B, and kk - below of bin B.
+        uint32_t *gh = ws.ghist + q * kBins;
+        for (int b = tid; b <= (int)B; b += kSmallThreads) {
+            const uint32_t c = b < (int)B ? hist[b] : kk - below;
+            if (c) atomicAdd(&gh[b], c);
+        }
+        uint32_t T = B, c_lt = below;
+        if (hshift > 0) {  // exact value inside bin B
+            __syncthreads();
+            for (int i = tid; i < kBins; i += kSmallThreads) hist[i] = 0;
+            __syncthreads();
+            const uint32_t mask = (1u << hshift) - 1u;
+            for (int e = tid; e < L; e += kSmallThreads) {
+                const uint32_t v = sums_s[e];
+                if (v != kPad && (v >> hshift) == B) atomicAdd(&hist[v & mask], 1u);
+            }
+            __syncthreads();
+            uint32_t below2;
+            const uint32_t f = small_find(hist, kk - below, misc, wsum, below2);
+            T = (B << hshift) | f;
+            c_lt = below + below2;
+        }
+        const int64_t base = b0 * kBlockVecs;
+        small_keep(L, T, kk - c_lt, s_of,
+                   [&](uint32_t pos, int e) { kept[pos] = ((uint64_t)sums_s[e] << 32) | (uint64_t)(base + e); },
+                   wsum);
+        // rank sort (keys are distinct): list position = number of smaller keys
+        for (int e = tid; e < (int)kk; e += kSmallThreads) {
+            const uint64_t key = kept[e];
+            int rank = 0;
+            for (int j = 0; j < (int)kk; ++j) rank += kept[j] < key ? 1 : 0;
+            mine[rank] = key;
+        }
+    }
+    if (tid == 0) {
+        ws.cnt[q * G + cta] = bad ? 0u : kk;
+        if (bad) atomicOr(&ws.status[q], 1u);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) misc[3] = (atomicAdd(&ws.ticket[q], 1u) == (uint32_t)(G - 1)) ? 1u : 0u;
+    __syncthreads();
+    if (misc[3] == 0) return;
+    __threadfence();
+
+    // ---- last CTA: merge the G sorted lists.  The histogram of all kept
+    // keys gives the k-th smallest s' of the union (T2) and the number below
+    // it (c2); each list then contributes a prefix: its keys below T2, and
+    // its keys equal to T2 while fewer than k - c2 such keys precede them in
+    // vector order (lists are in CTA order = vector order).
+    uint32_t *cnt_s = reinterpret_cast<uint32_t *>(region);  // [G] counts, [G] lt offsets, [G] eq offsets
+    uint32_t *lt_s = cnt_s + G;
+    uint32_t *eq_s = lt_s + G;
+    uint32_t *lc_s = eq_s + G;  // [G] keys below T2 per list
+    uint64_t *all = reinterpret_cast<uint64_t *>(region + small_align_dev((size_t)G * 16, 16));
+    const uint32_t slot_bytes = (uint32_t)(((size_t)G * k * 8 + 15) & ~(size_t)15);
+    uint64_t *mbar = bars + nch;  // fresh barrier for the merge copies
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+        // the lists and the histogram were written by other CTAs, and this
+        // CTA's shared memory was last used, through the generic proxy
+        asm volatile("fence.proxy.async;" ::: "memory");
+        mbar_arrive_expect_tx(mbar, slot_bytes + kBins * 4);
+        bulk_g2s(all, ws.keys + q * qstride, slot_bytes, mbar);
+        bulk_g2s(hist, ws.ghist + q * kBins, kBins * 4, mbar);
+    }
+    if (tid < G) cnt_s[tid] = __ldcg(ws.cnt + q * G + tid);
+    __syncthreads();
+    const bool copied = mbar_wait_bounded(mbar, 0u, kSmallWait);
+    if (!copied) atomicOr(&misc[2], 2u);
+    __syncthreads();
+    const bool qbad = (misc[2] & 2u) != 0u || __ldcg(&ws.status[q]) != 0u;
+    if (misc[2] & 2u) {
+        if (tid == 0) mbar_wait_bounded(mbar, 0u, kSmallWait / 10);  // bounded: let a late copy land
+        __syncthreads();
+    }
+    uint32_t total = 0;
+    small_scan(tid < G ? cnt_s[tid] : 0u, wsum, total);
+    const int kout = qbad ? 0 : (int)min((uint32_t)k, total);
+    uint64_t *fin = all + (size_t)G * k;
+    fin = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(fin) + 31) & ~uintptr_t(15));
+    // first position in list c whose s' (or s' >> sh) is >= v
+    auto lower = [&](int c, uint32_t v, int sh) -> uint32_t {
+        const uint64_t *lst = all + (size_t)c * k;
+        uint32_t lo = 0, hi = cnt_s[c];
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (((uint32_t)(lst[mid] >> 32) >> sh) < v) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    if (kout > 0) {
+        uint32_t below;
+        const uint32_t B2 = small_find(hist, (uint32_t)kout, misc, wsum, below);
+        uint32_t T2 = B2, c2 = below;
+        if (hshift > 0) {  // exact value inside bin B2: count the bin's keys by value
+            const uint32_t mask = (1u << hshift) - 1u;
+            for (int i = tid; i < kBins; i += kSmallThreads) hist[i] = 0;
+            __syncthreads();
+            for (int c = warp; c < G; c += kSmallWarps) {
+                const uint32_t lo = lower(c, B2, hshift), hi = lower(c, B2 + 1, hshift);
+                for (uint32_t j = lo + lane; j < hi; j += 32)
+                    atomicAdd(&hist[(uint32_t)(all[(size_t)c * k + j] >> 32) & mask], 1u);
+            }
+            __syncthreads();
+            uint32_t below2;
+            const uint32_t f = small_find(hist, (uint32_t)kout - below, misc, wsum, below2);
+            T2 = (B2 << hshift) | f;
+            c2 = below + below2;
+        }
+        const uint32_t r = (uint32_t)kout - c2;  // keys equal to T2 to keep, lowest index first
+        uint32_t lt = 0, eq = 0;
+        if (tid < G) {
+            lt = lower(tid, T2, 0);
+            eq = lower(tid, T2 + 1, 0) - lt;
+            lc_s[tid] = lt;
+        }
+        uint32_t t1, t2;
+        const uint32_t lt_off = small_scan(lt, wsum, t1);
+        const uint32_t eq_off = small_scan(eq, wsum, t2);
+        if (tid < G) {
+            lt_s[tid] = lt_off;
+            eq_s[tid] = eq_off;
+        }
+        __syncthreads();
+        for (int c = warp; c < G; c += kSmallWarps) {
+            const uint64_t *lst = all + (size_t)c * k;
+            const uint32_t nlt = lc_s[c], lo = lt_s[c], eo = eq_s[c];
+            const uint32_t neq = eo < r ? min(r - eo, (c + 1 < G ? eq_s[c + 1] : t2) - eo) : 0u;
+            for (uint32_t j = lane; j < nlt; j += 32) fin[lo + j] = lst[j];
+            for (uint32_t j = lane; j < neq; j += 32) fin[c2 + eo + j] = lst[nlt + j];
+        }
+        __syncthreads();
+    }
+    // order the kout survivors by (s', index): rank counting for small k, bitonic otherwise
+    int P = 1;
+    while (P < kout) P <<= 1;
+    if (kout <= 256) {
+        uint64_t *sorted = fin + P;
+        for (int e = tid; e < kout; e += kSmallThreads) {
+            const uint64_t key = fin[e];
+            int rank = 0;
+            for (int j = 0; j < kout; ++j) rank += fin[j] < key ? 1 : 0;
+            sorted[rank] = key;
+        }
+        __syncthreads();
+        fin = sorted;
+    } else {
+        for (int i = kout + tid; i < P; i += kSmallThreads) fin[i] = ~0ull;
+        __syncthreads();
+        for (int size = 2; size <= P; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = tid; i < P / 2; i += kSmallThreads) {
+                    const int lo = 2 * i - (i & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool asc = (lo & size) == 0;
+                    const uint64_t a = fin[lo], b = fin[hi];
+                    if ((a > b) == asc) {
+                        fin[lo] = b;
+                        fin[hi] = a;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    for (int r = tid; r < k; r += kSmallThreads) {
+        if (r < kout) {
+            const uint32_t sp = (uint32_t)(fin[r] >> 32);
+            out_sums[q * k + r] = (uint16_t)(metric == BOLT_METRIC_DOT ? smax - sp : sp);
+            out_idx[q * k + r] = qbad ? -2 : (int64_t)(uint32_t)fin[r];
+        } else {
+            out_sums[q * k + r] = 0;
+            out_idx[q * k + r] = qbad ? -2 : -1;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+static size_t small_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Fills the small-path fields of plan if this size class applies.
+bool plan_topk_small(int64_t n, int32_t M, int32_t k, int sms, TopkPlan *plan) {
+    const int64_t nb = num_blocks(n);
+    if (nb == 0 || sms <= 0 || k > kMaxSmallK) return false;
+    int64_t G = sms;
+    if (G > nb) G = nb;
+    if (G > kSmallMergeKeys / k) G = kSmallMergeKeys / k;
+    if (G < 1 || G > kSmallThreads) return false;
+    const int64_t nbc = (nb + G - 1) / G;
+    G = (nb + nbc - 1) / nbc;  // every CTA gets at least one block
+    int P = 1;
+    while (P < k) P <<= 1;
+    const int nch = (int)((nbc + kSmallChunk - 1) / kSmallChunk);
+    const size_t scan_region = small_align((size_t)nbc * M * kRowBytes + (size_t)nbc * kBlockVecs * 2, 16) +
+                               (size_t)k * 8;
+    const size_t merge_region = small_align((size_t)G * 16, 16) + small_align((size_t)G * k * 8, 16) + 32 +
+                                (size_t)2 * P * 8;
+    const size_t region = scan_region > merge_region ? scan_region : merge_region;
+    const size_t smem = (size_t)kBins * 4 + kSmallMiscWords * 4 + small_align((size_t)M * 16, 16) +
+                        (size_t)((nch + 2) / 2 * 2) * 8 + region;
+    if (smem > kSmallMaxSmem) return false;
+    int hshift = 0;
+    while (((255 * M) >> hshift) >= kBins) ++hshift;
+    plan->small = 1;
+    plan->grid = (int)G;
+    plan->nbc = (int)nbc;
+    plan->hshift = hshift;
+    plan->smem_bytes = smem;
+    return true;
+}
+
+// ticket, status and histograms: zeroed before every launch
+static size_t topk_small_header_bytes(int64_t nq) {
+    return small_align((size_t)nq * 8, 256) + (size_t)nq * kBins * 4;
+}
+
+int64_t topk_small_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k) {
+    const size_t qstride = ((size_t)plan.grid * k + 1) & ~(size_t)1;
+    return (int64_t)(topk_small_header_bytes(nq) + small_align((size_t)nq * plan.grid * 4, 256) +
+                     (size_t)nq * qstride * 8);
+}
+
+template <int MT>
+static int launch_small_w(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, int32_t k,
+                          int32_t metric, uint16_t *out_sums, int64_t *out_idx, const SmallWS &w,
+                          const TopkPlan &plan, cudaStream_t stream) {
+    auto kern = topk_small_kernel<MT>;
+    int rc = ensure_smem((const void *)kern, plan.smem_bytes);
+    if (rc) return rc;
+    dim3 grid(plan.grid, (unsigned)nq);
+    kern<<<grid, kSmallThreads, plan.smem_bytes, stream>>>(reinterpret_cast<const uint32_t *>(codes), n, M, luts, k,
+                                                            metric, w, plan.nbc, plan.hshift, out_sums, out_idx);
+    return check_launch("topk_small_kernel");
+}
+
+int launch_topk_small(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, int32_t k,
+                      int32_t metric, uint16_t *out_sums, int64_t *out_idx, void *workspace, const TopkPlan &plan,
+                      cudaStream_t stream) {
+    BOLT_REQUIRE(nq <= 65535, BOLT_EUNSUPPORTED, "nq=%lld > 65535 per call", (long long)nq);
+    BOLT_CUDA(cudaMemsetAsync(workspace, 0, topk_small_header_bytes(nq), stream));
+    uint8_t *p = static_cast<uint8_t *>(workspace);
+    SmallWS w;
+    w.ticket = reinterpret_cast<uint32_t *>(p);
+    w.status = w.ticket + nq;
+    w.ghist = reinterpret_cast<uint32_t *>(p + small_align((size_t)nq * 8, 256));
+    p += topk_small_header_bytes(nq);
+    w.cnt = reinterpret_cast<uint32_t *>(p);
+    p += small_align((size_t)nq * plan.grid * 4, 256);
+    w.keys = reinterpret_cast<uint64_t *>(p);
+#define BOLT_SMALL_ARGS codes, n, M, luts, nq, k, metric, out_sums, out_idx, w, plan, stream
+    if (M == 8) return launch_small_w<8>(BOLT_SMALL_ARGS);
+    if (M == 16) return launch_small_w<16>(BOLT_SMALL_ARGS);
+    if (M == 32) return launch_small_w<32>(BOLT_SMALL_ARGS);
+    return launch_small_w<0>(BOLT_SMALL_ARGS);
+#undef BOLT_SMALL_ARGS
+}
+
+}  // namespace bolt

@@ -4,7 +4,10 @@
 and runs, in order (all in libbolt.so kernels):
   1. encode the database (Sec. 3.1 h, K = 16),
   2. build the uint8 query tables for each metric (Sec. 3.1 g, Sec. 3.2 beta),
-  3. scan + exact top-k, one query per launch (the plain GPU form),
+  3. scan + exact top-k, one query per launch (the plain GPU form); the
+     launches go round-robin to ``streams`` CUDA streams, each with its own
+     workspace, so the next query's scan can start on the SMs that the
+     previous query's final merge leaves idle,
   4. dequantize the k best sums to distances / inner products (Sec. 3.2).
 The launch sequence is captured once into a CUDA graph and replayed, so the
 per-launch host overhead of the thousands of small launches is paid once.
@@ -18,7 +21,7 @@ from . import bolt
 
 class SearchStep:
     def __init__(self, n, J, M, nq, k, centroids, quant, metrics=(bolt.METRIC_L2, bolt.METRIC_DOT),
-                 precision=bolt.PREC_FP32, device="cuda"):
+                 precision=bolt.PREC_FP32, device="cuda", streams=3):
         self.n, self.J, self.M, self.nq, self.k = n, J, M, nq, k
         self.metrics = tuple(metrics)
         self.quant = dict(quant)  # metric -> (a, b)
@@ -32,7 +35,9 @@ class SearchStep:
         self.sums = {m: torch.empty((nq, k), dtype=torch.uint16, device=dev) for m in self.metrics}
         self.idx = {m: torch.empty((nq, k), dtype=torch.int64, device=dev) for m in self.metrics}
         self.dist = {m: torch.empty((nq, k), dtype=torch.float32, device=dev) for m in self.metrics}
-        self.ws = torch.empty(bolt.topk_workspace_bytes(n, M, 1, k), dtype=torch.uint8, device=dev)
+        self.side = [torch.cuda.Stream(device=dev) for _ in range(max(1, streams))]
+        self.ws = [torch.empty(bolt.topk_workspace_bytes(n, M, 1, k), dtype=torch.uint8, device=dev)
+                   for _ in self.side]
         self.graphs = None
         self.launches_per_step = 1 + len(self.metrics) * (2 + nq)
         self.timing = []  # (start, end) event pairs around each top-k segment
@@ -50,9 +55,16 @@ class SearchStep:
             bolt.build_luts(self.Q, self.C, m, a, b, out=self.luts[m])
 
     def _topk(self, m):
+        cur = torch.cuda.current_stream()
+        for s in self.side:
+            s.wait_stream(cur)
         for q in range(self.nq):
+            i = q % len(self.side)
             bolt.topk(self.codes, self.n, self.M, self.luts[m][q:q + 1], self.k, m,
-                      out_sums=self.sums[m][q:q + 1], out_idx=self.idx[m][q:q + 1], workspace=self.ws)
+                      out_sums=self.sums[m][q:q + 1], out_idx=self.idx[m][q:q + 1], workspace=self.ws[i],
+                      stream=self.side[i])
+        for s in self.side:
+            cur.wait_stream(s)
 
     def _post(self):
         for m in self.metrics:
@@ -99,9 +111,40 @@ class SearchStep:
                 g.replay()
         self.graphs[-1].replay()
 
+    def serial_topk_ms(self, launches=20, reps=10, metric=bolt.METRIC_L2):
+        """Device time of one top-k launch by itself: `launches` launches on
+        one stream, captured in a CUDA graph and replayed `reps` times
+        between two events."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+
+        def body():
+            for q in range(launches):
+                qq = q % self.nq
+                bolt.topk(self.codes, self.n, self.M, self.luts[metric][qq:qq + 1], self.k, metric,
+                          out_sums=self.sums[metric][qq:qq + 1], out_idx=self.idx[metric][qq:qq + 1],
+                          workspace=self.ws[0], stream=s)
+
+        with torch.cuda.stream(s):
+            body()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+            body()
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / (reps * launches)
+
     def topk_ms_per_launch(self):
-        """Mean duration of one top-k launch over the timed replays (call
-        after synchronizing)."""
+        """Step time of the top-k segments divided by their launches (call
+        after synchronizing): with launches overlapping on several streams
+        this is the time per query of the step, not one launch's duration."""
         if not self.timing:
             return float("nan")
         tot = sum(e0.elapsed_time(e1) for e0, e1 in self.timing)

@@ -185,7 +185,8 @@ def check_topk(torch, codes, luts, k, metric, workspace=None):
 @pytest.mark.parametrize("n,M,k", [(5, 4, 10), (256, 8, 1), (1000, 8, 10), (10_003, 16, 100), (70_000, 16, 37),
                                    (1539, 16, 10), (100_003, 16, 100), (25_603, 8, 64),
                                    (200_000, 8, 100), (50_000, 32, 1000), (20_000, 64, 50), (3000, 128, 20),
-                                   (600, 256, 5)])
+                                   (600, 256, 5), (6_000_000, 16, 100), (3_000_000, 32, 10),
+                                   (2_600_000, 8, 1024), (400_000, 64, 50)])
 def test_topk_bitexact(torch_cuda, metric, n, M, k):
     rng = np.random.default_rng(n * 7 + M + k + metric)
     codes = rng.integers(0, 16, (n, M)).astype(np.uint8)

@@ -111,9 +111,11 @@ def test_tight_budget_serializes_but_results_hold(torch_cuda, world):
     for memory, the books never exceed the budget, results are unchanged."""
     torch = torch_cuda
     resident = sum(w["codes"].numel() + w["Cd"].numel() * 4 for w in world.values())
-    budget = resident + (10 << 20)
-    srv = make_server(torch, world, budget=budget, slots=4)
     reqs = make_trace(6, 60, rate=5000.0)
+    probe = make_server(torch, world, budget=2 << 30, slots=1)
+    largest = max(serve.batch_bytes(probe.collections[r.collection], r.kind, r.nq, r.k) for r in reqs)
+    budget = resident + largest + (1 << 20)
+    srv = make_server(torch, world, budget=budget, slots=4)
     done = serve.run_trace(srv, reqs)
     assert len(done) == len(reqs)
     assert srv.budget.peak <= budget
