@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--graph-reps", type=int, default=0, help="also time graph replays of the launches")
     ap.add_argument("--collections", type=int, default=64, help="--only batch: first N collections")
+    ap.add_argument("--topk-streams", type=int, default=3, help="streams the step's one-query launches use")
     return ap.parse_args()
 
 
@@ -534,7 +535,8 @@ def run_reference(args, world, rank):
 def config_dict(cfg):
     return {"workload": "mixture_1m", "n": cfg["n"], "dims": cfg["J"], "codebooks": cfg["M"],
             "code_bytes_per_vector": cfg["M"] // 2, "queries": cfg["nq"], "k": cfg["k"],
-            "metrics": ["l2", "dot"], "launch": "one query per launch (CUDA graph replay; launches round-robin on 3 streams)",
+            "metrics": ["l2", "dot"], "launch": "one query per launch (CUDA graph replay; launches round-robin on several streams, "
+                      "topk_streams)",
             "l2_cache": "inputs larger than L2: 512 MB fp32 database encoded every step"}
 
 
@@ -550,7 +552,7 @@ def run_bolt(args, world, rank, local):
     cfg = workload(args.nq)
     n, J, M, nq, k = cfg["n"], cfg["J"], cfg["M"], cfg["nq"], cfg["k"]
     X, Q, Xd, Qd, C, quant = prepare(cfg, data_seed=rank)
-    step = SearchStep(n, J, M, nq, k, C, quant)
+    step = SearchStep(n, J, M, nq, k, C, quant, streams=args.topk_streams)
     step.set_inputs(Xd, Qd)
     step.capture()
 
