@@ -275,11 +275,13 @@ template <int WARPS, int MT, int BPI>
 __global__ void __launch_bounds__(WARPS * 32, 1)
     topk_kernel(const uint32_t *__restrict__ codes, int64_t n, int32_t M, const uint8_t *__restrict__ luts,
                 int32_t k, int32_t metric, TopkWS ws, int stages, int cap, int hshift, int64_t blocks_per_cta,
-                int out_cap, uint16_t *__restrict__ out_sums, int64_t *__restrict__ out_idx) {
+                int out_cap, uint16_t *__restrict__ out_sums, int64_t *__restrict__ out_idx,
+                const uint32_t *__restrict__ active) {
     constexpr int T = WARPS * 32;
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t q = blockIdx.y;
+    if (active != nullptr && active[q] == 0u) return;  // only the queries marked for this kernel
     const int G = gridDim.x, cta = blockIdx.x;
     if (MT > 0) M = MT;
     const uint32_t blk_bytes = (uint32_t)M * kRowBytes;
@@ -518,9 +520,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             st = 0;
             par ^= 1u;
         }
-        uint32_t pk[BPI][4];
-        uint32_t thr = vmisc[1];
-        bool maybe = false;
+        uint32_t pk[BPI][4], sw[BPI][4];
         uint32_t v0[BPI];
         bool tail[BPI], valid[BPI];
 #pragma unroll
@@ -537,22 +537,57 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
                 e_hi = smax2 - e_hi;
                 o_hi = smax2 - o_hi;
             }
-            bool mh = valid[h];
-            if (swar && thr <= 0x7FFFu) {
-                // s' < 2^15: the top bit of (s' + 2^15 - thr) in each lane is
-                // clear exactly when s' < thr, with no borrow between lanes.
-                const uint32_t nt2 = 0u - (thr | (thr << 16));
-                const uint32_t d = imad(e_lo | 0x80008000u, one, nt2) & imad(o_lo | 0x80008000u, one, nt2) &
-                                   imad(e_hi | 0x80008000u, one, nt2) & imad(o_hi | 0x80008000u, one, nt2);
-                mh = mh && (~d & 0x80008000u) != 0u;
-            }
-            if (tail[h]) mh = mh && v0[h] < (uint32_t)n;
-            maybe = maybe || mh;
+            sw[h][0] = e_lo;
+            sw[h][1] = o_lo;
+            sw[h][2] = e_hi;
+            sw[h][3] = o_hi;
             const uint4 q4 = pack_sums(e_lo, o_lo, e_hi, o_hi);
             pk[h][0] = q4.x;
             pk[h][1] = q4.y;
             pk[h][2] = q4.z;
             pk[h][3] = q4.w;
+        }
+        uint32_t thr = vmisc[1];
+        if (j == 0 && thr == kThrAll) {
+            // Seed the threshold from this warp's first unit: its k-th
+            // smallest s' (T) has k vectors at or below it, so no vector with
+            // s' > T can enter the top k (binary search on T, warp-wide counts).
+            auto count_le = [&](uint32_t t) -> uint32_t {
+                uint32_t c = 0;
+#pragma unroll
+                for (int h = 0; h < BPI; ++h)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const uint32_t sp = (pk[h][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                        c += (valid[h] && (!tail[h] || v0[h] + i < (uint32_t)n) && sp <= t) ? 1u : 0u;
+                    }
+                return __reduce_add_sync(0xFFFFFFFFu, c);
+            };
+            if (count_le(0xFFFFu) >= (uint32_t)k) {
+                uint32_t lo = 0, hi = smax;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (count_le(mid) >= (uint32_t)k) hi = mid;
+                    else lo = mid + 1;
+                }
+                if (lane == 0) atomicMin(&misc[1], lo + 1u);
+                thr = min(thr, lo + 1u);
+            }
+        }
+        bool maybe = false;
+#pragma unroll
+        for (int h = 0; h < BPI; ++h) {
+            bool mh = valid[h];
+            if (swar && thr <= 0x7FFFu) {
+                // s' < 2^15: the top bit of (s' + 2^15 - thr) in each lane is
+                // clear exactly when s' < thr, with no borrow between lanes.
+                const uint32_t nt2 = 0u - (thr | (thr << 16));
+                const uint32_t d = imad(sw[h][0] | 0x80008000u, one, nt2) & imad(sw[h][1] | 0x80008000u, one, nt2) &
+                                   imad(sw[h][2] | 0x80008000u, one, nt2) & imad(sw[h][3] | 0x80008000u, one, nt2);
+                mh = mh && (~d & 0x80008000u) != 0u;
+            }
+            if (tail[h]) mh = mh && v0[h] < (uint32_t)n;
+            maybe = maybe || mh;
         }
         if (__any_sync(0xFFFFFFFFu, maybe)) {
             for (int attempt = 0;; ++attempt) {
@@ -726,11 +761,21 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
 // ------------------------------------------------------------------ host side
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-int plan_topk(int64_t n, int32_t M, int32_t k, TopkPlan *plan) {
+int plan_topk(int64_t n, int32_t M, int32_t k, int64_t nq, TopkPlan *plan) {
     BOLT_REQUIRE(k >= 1 && k <= kMaxK, BOLT_EUNSUPPORTED, "k=%d outside [1, %d]", k, kMaxK);
     plan->small = 0;
     plan->nbc = 0;
+    plan->mq = 0;
     if (plan_topk_small(n, M, k, device_sm_count(), plan)) return BOLT_OK;
+    int rc = plan_topk_stream(n, M, k, plan);
+    if (rc) return rc;
+    // several queries share each code pass in the multi-query pipeline; a
+    // single query is faster in the fused streaming kernel
+    if (n > 0 && nq >= kMqMinQueries) plan_topk_mq(n, M, k, device_sm_count(), plan);
+    return BOLT_OK;
+}
+
+int plan_topk_stream(int64_t n, int32_t M, int32_t k, TopkPlan *plan) {
     // Two blocks per unit of work for small M on large databases (amortizes
     // per-unit overhead once every warp has many blocks to stream).
     const int64_t blocks_per_warp = num_blocks(n) / ((int64_t)(device_sm_count() > 0 ? device_sm_count() : 1) * 16);
@@ -777,6 +822,12 @@ size_t topk_header_bytes(int64_t nq) { return align_up((size_t)nq * 12, 256) + (
 
 int64_t topk_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k) {
     if (plan.small) return topk_small_workspace_bytes(plan, nq, k);
+    if (plan.mq) return topk_mq_workspace_bytes(plan, nq, k);
+    return topk_stream_workspace_bytes(plan, nq, k);
+}
+
+int64_t topk_stream_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k) {
+    (void)k;
     return (int64_t)(topk_header_bytes(nq) + (size_t)nq * plan.list_cap * 8);
 }
 
@@ -798,14 +849,15 @@ TopkWS carve_topk_ws(void *ws, const TopkPlan &plan, int64_t nq, int32_t k) {
 template <int WARPS, int MT, int BPI>
 static int launch_w(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, int32_t k,
                     int32_t metric, uint16_t *out_sums, int64_t *out_idx, const TopkWS &w, const TopkPlan &plan,
-                    cudaStream_t stream) {
+                    const uint32_t *active, cudaStream_t stream) {
     auto kern = topk_kernel<WARPS, MT, BPI>;
     int rc = ensure_smem((const void *)kern, plan.smem_bytes);
     if (rc) return rc;
     dim3 grid(plan.grid, (unsigned)nq);
     kern<<<grid, WARPS * 32, plan.smem_bytes, stream>>>(reinterpret_cast<const uint32_t *>(codes), n, M, luts, k,
                                                          metric, w, plan.stages, plan.cap, plan.hshift,
-                                                         plan.blocks_per_cta, plan.out_cap, out_sums, out_idx);
+                                                         plan.blocks_per_cta, plan.out_cap, out_sums, out_idx,
+                                                         active);
     return check_launch("topk_kernel");
 }
 
@@ -814,10 +866,17 @@ int launch_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts,
                 cudaStream_t stream) {
     if (plan.small) return launch_topk_small(codes, n, M, luts, nq, k, metric, out_sums, out_idx, workspace, plan,
                                              stream);
+    if (plan.mq) return launch_topk_mq(codes, n, M, luts, nq, k, metric, out_sums, out_idx, workspace, plan, stream);
+    return launch_topk_stream(codes, n, M, luts, nq, k, metric, out_sums, out_idx, workspace, plan, nullptr, stream);
+}
+
+int launch_topk_stream(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, int32_t k,
+                       int32_t metric, uint16_t *out_sums, int64_t *out_idx, void *workspace, const TopkPlan &plan,
+                       const uint32_t *active, cudaStream_t stream) {
     BOLT_REQUIRE(nq <= 65535, BOLT_EUNSUPPORTED, "nq=%lld > 65535 per call", (long long)nq);
     BOLT_CUDA(cudaMemsetAsync(workspace, 0, topk_header_bytes(nq), stream));
     const TopkWS w = carve_topk_ws(workspace, plan, nq, k);
-#define BOLT_TOPK_ARGS codes, n, M, luts, nq, k, metric, out_sums, out_idx, w, plan, stream
+#define BOLT_TOPK_ARGS codes, n, M, luts, nq, k, metric, out_sums, out_idx, w, plan, active, stream
     if (plan.warps == 16) {
         if (M == 8) return plan.bpi == 2 ? launch_w<16, 8, 2>(BOLT_TOPK_ARGS) : launch_w<16, 8, 1>(BOLT_TOPK_ARGS);
         if (M == 16) return plan.bpi == 2 ? launch_w<16, 16, 2>(BOLT_TOPK_ARGS) : launch_w<16, 16, 1>(BOLT_TOPK_ARGS);
@@ -838,7 +897,7 @@ int64_t bolt_topk_workspace_bytes(int64_t n, int32_t M, int64_t nq, int32_t k) {
     bolt::clear_error();
     if (bolt::check_nm(n, M) || nq < 0) return -1;
     bolt::TopkPlan plan;
-    if (bolt::plan_topk(n, M, k, &plan)) return -1;
+    if (bolt::plan_topk(n, M, k, nq, &plan)) return -1;
     return bolt::topk_workspace_bytes(plan, nq, k);
 }
 
@@ -851,7 +910,7 @@ int bolt_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, i
     BOLT_REQUIRE(nq >= 0, BOLT_EINVAL, "nq=%lld < 0", (long long)nq);
     BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT, BOLT_EINVAL, "bad metric %d", metric);
     bolt::TopkPlan plan;
-    rc = bolt::plan_topk(n, M, k, &plan);
+    rc = bolt::plan_topk(n, M, k, nq, &plan);
     if (rc) return rc;
     if (nq == 0) return BOLT_OK;
     BOLT_REQUIRE(luts && out_sums && out_idx && (codes || n == 0), BOLT_EINVAL, "null pointer");
@@ -919,7 +978,7 @@ extern "C" int bolt_topk_noalloc(const uint8_t *codes, int64_t n, int32_t M, con
     BOLT_REQUIRE(nq >= 0, BOLT_EINVAL, "nq=%lld < 0", (long long)nq);
     BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT, BOLT_EINVAL, "bad metric %d", metric);
     bolt::TopkPlan plan;
-    rc = bolt::plan_topk(n, M, k, &plan);
+    rc = bolt::plan_topk(n, M, k, nq, &plan);
     if (rc) return rc;
     if (nq == 0) return BOLT_OK;
     BOLT_REQUIRE(luts && out_sums && out_idx && (codes || n == 0), BOLT_EINVAL, "null pointer");

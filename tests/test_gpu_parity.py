@@ -195,6 +195,22 @@ def test_topk_bitexact(torch_cuda, metric, n, M, k):
 
 
 @pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
+@pytest.mark.parametrize("hi,nq", [(2, 4), (16, 5), (256, 37), (16, 1), (2, 1)])
+def test_topk_large_database_paths(torch_cuda, metric, hi, nq):
+    """3,000,000 vectors (beyond the shared-memory size class).  With 4 or
+    more queries: sample bound, multi-query filter and select, tables drawn
+    from [0, hi): hi = 2 makes every sum tie (candidate overflow: the exact
+    streaming fallback runs), hi = 16 makes hundreds of ties at the k-th sum
+    (ordered by index), hi = 256 is the ordinary case; 37 queries span tiles
+    of 16, 16, 4 and 1.  One query: the fused streaming kernel."""
+    rng = np.random.default_rng(hi * 10 + nq + metric)
+    n, M, k = 3_000_000, 16, 100
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+    luts = rng.integers(0, hi, (nq, M, 16)).astype(np.uint8)
+    check_topk(torch_cuda, codes, luts, k, metric)
+
+
+@pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
 def test_topk_heavy_ties(torch_cuda, metric):
     """Tables with 2 distinct values: huge tie groups decided by index."""
     rng = np.random.default_rng(3)
