@@ -295,7 +295,7 @@ def large_n_scan(codes, C, quant, hbm_peak, peak_kind):
                                  "speedup_vs_one_query_launches": round(ms * 64 / ms_b, 2)}}
 
 
-def serving(codes50, C, quant, count=300, rate=40.0, slots=4, budget_gb=16.0):
+def serving(codes50, C, quant, count=300, rates=(40.0, 80.0), slots=4, budget_gb=16.0):
     """Serving trace on the resident 50M-vector database plus the encoded
     100,000 x 512 matmul operand (M = 32): Poisson arrivals, 1..512 queries
     per request, L2 / dot, k 10..100, 10% approximate-matmul requests
@@ -313,39 +313,56 @@ def serving(codes50, C, quant, count=300, rate=40.0, slots=4, budget_gb=16.0):
                                     .contiguous(), metric=bolt.METRIC_DOT)
     codesB = bolt.encode(B, CB)
     del B
-    trace = synth.poisson_trace(11, count, rate, cfg["J"], matmul_frac=0.1, J_mm=mm["J"])
-
-    def requests():
-        return [serve.Request(i, "B" if r["kind"] == "matmul" else "db", r["Q"], kind=r["kind"],
-                              metric=r["metric"], k=r["k"], t_arrival=r["t_arrival"]) for i, r in enumerate(trace)]
-
     srv = serve.Server(int(budget_gb * 2**30), slots=slots)
     srv.add_collection("db", codes50, cfg["n"], cfg["M"], C, quant)
     srv.add_collection("B", codesB, mm["n"], mm["M"], CB, {bolt.METRIC_DOT: (aB, bB), bolt.METRIC_L2: (aB, bB)})
     n_of = {"db": cfg["n"], "B": mm["n"]}
-    # warm-up: a few requests through both forms (kernel attributes, pinned buffers)
-    warm = requests()[:6]
-    for r in warm:
-        r.t_arrival = 0.0
-    serve.run_trace(srv, warm)
-    serve.run_plain(srv.collections, requests()[:2])
-    torch.cuda.synchronize()
-    got = serve.run_trace(srv, requests())
-    srv_stats = serve.latency_stats(got, n_of)
-    srv_stats.update(batches=srv.batches, launches=srv.launches, slots=slots,
-                     budget_bytes=srv.budget.total, peak_budget_bytes=srv.budget.peak)
-    plain = serve.run_plain(srv.collections, requests())
-    plain_stats = serve.latency_stats(plain, n_of)
-    by = {r.rid: r for r in plain}
-    same = all((np.array_equal(r.out, by[r.rid].out) if r.kind == "matmul" else
-                (np.array_equal(r.idx, by[r.rid].idx) and np.array_equal(r.dist, by[r.rid].dist))) for r in got)
+    out = {"workload": "serve_50m: resident 50,000,000 x 128 (M=16, 400 MB codes) + matmul B 100,000 x 512 "
+                       "(M=32); %d Poisson requests per rate, 1-512 queries (log-uniform), L2/dot, k 10-100, "
+                       "10%% matmul (1-512 rows of A)" % count,
+           "latency": "host time from scheduled arrival to results in host memory", "rates": []}
+    for rate in rates:
+        trace = synth.poisson_trace(11, count, rate, cfg["J"], matmul_frac=0.1, J_mm=mm["J"])
+
+        def requests():
+            return [serve.Request(i, "B" if r["kind"] == "matmul" else "db", r["Q"], kind=r["kind"],
+                                  metric=r["metric"], k=r["k"], t_arrival=r["t_arrival"])
+                    for i, r in enumerate(trace)]
+
+        # warm-up: a few requests through both forms (kernel attributes, pinned buffers)
+        warm = requests()[:6]
+        for r in warm:
+            r.t_arrival = 0.0
+        serve.run_trace(srv, warm)
+        serve.run_plain(srv.collections, requests()[:2])
+        torch.cuda.synchronize()
+        b0, l0 = srv.batches, srv.launches
+        got = serve.run_trace(srv, requests())
+        srv_stats = serve.latency_stats(got, n_of)
+        srv_stats.update(batches=srv.batches - b0, slots=slots, budget_bytes=srv.budget.total,
+                         peak_budget_bytes=srv.budget.peak)
+        plain = serve.run_plain(srv.collections, requests())
+        plain_stats = serve.latency_stats(plain, n_of)
+        by = {r.rid: r for r in plain}
+        diff = []
+        for r in got:
+            p = by[r.rid]
+            if r.kind == "matmul":
+                if not np.array_equal(r.out, p.out):
+                    diff.append({"rid": r.rid, "kind": "matmul", "rows": r.nq, "batch": r.batch_id,
+                                 "elements": int((r.out != p.out).sum())})
+            else:
+                rows = (r.idx != p.idx).any(axis=1) | (r.dist != p.dist).any(axis=1)
+                if rows.any():
+                    diff.append({"rid": r.rid, "kind": "search", "nq": r.nq, "k": r.k, "metric": r.metric,
+                                 "batch": r.batch_id, "rows": int(rows.sum())})
+        out["rates"].append({"rate_per_s": rate, "offered_queries_per_s": sum(r["nq"] for r in trace) /
+                             trace[-1]["t_arrival"], "server": srv_stats,
+                             "plain_one_query_per_launch": plain_stats, "results_identical": not diff,
+                             "mismatches": diff[:10]})
     del srv, codesB
     torch.cuda.empty_cache()
-    return {"workload": "serve_50m: resident 50,000,000 x 128 (M=16, 400 MB codes) + matmul B 100,000 x 512 "
-                        "(M=32); %d Poisson requests at %.0f/s, 1-512 queries (log-uniform), L2/dot, k 10-100, "
-                        "10%% matmul (1-512 rows of A)" % (count, rate),
-            "server": srv_stats, "plain_one_query_per_launch": plain_stats, "results_identical": bool(same),
-            "latency": "host time from scheduled arrival to results in host memory"}
+    return out
 
 
 def encode_10m():
