@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-aux", action="store_true", help="skip the large-N and encode side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["topk1m", "topk50m", "topk8m_batch64", "encode10m", "encode10m_tc", "batch", "serve",
-                             "large50m"], default=None,
+                             "large50m", "accuracy"], default=None,
                     help="profiling run: set up one workload and launch only its kernel a few times")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--graph-reps", type=int, default=0, help="also time graph replays of the launches")
@@ -240,6 +240,51 @@ def build_50m(C):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     return codes
+
+
+def accuracy_report(Xd, C, quant, nq=200, seed=21):
+    """Accuracy on the 1M mixture (the paper's Recall@R, Sec. 4.5, and
+    dot-product correlation, Sec. 4.6): for nq held-out mixture queries, the
+    fraction whose true nearest neighbour (fp64 brute force) is among the R
+    best by Bolt's uint8-table sums and by the fp32-table sums ("Bolt No
+    Quantize"); and the Pearson correlation of dequantized approximate dot
+    products with the true ones over a sample of pairs."""
+    import torch
+
+    from paper_1706_10283_gb300 import bolt, synth
+
+    n, J = Xd.shape
+    M = C.shape[0]
+    Q = synth.mixture_torch(nq, J, seed=seed)
+    codes = bolt.encode(Xd, C)
+    a, b = quant[bolt.METRIC_L2]
+    luts, luts32 = bolt.build_luts(Q, C, bolt.METRIC_L2, a, b, out_f32=True)
+    # ground truth: fp64 brute force nearest neighbour
+    X64 = Xd.double()
+    true_nn = []
+    for lo in range(0, nq, 50):
+        q64 = Q[lo:lo + 50].double()
+        d = (q64 * q64).sum(1, keepdim=True) - 2 * q64 @ X64.T + (X64 * X64).sum(1)[None]
+        true_nn.append(d.argmin(1))
+    true_nn = torch.cat(true_nn)
+    del X64
+    Rs = (1, 10, 100)
+    out = {"queries": nq, "R": list(Rs)}
+    s_q, i_q = bolt.topk(codes, n, M, luts, max(Rs), bolt.METRIC_L2)
+    sf = bolt.scan_float(codes, n, M, luts32)
+    i_f = torch.topk(sf, max(Rs), dim=1, largest=False).indices
+    for name, idx in (("bolt_uint8_tables", i_q), ("bolt_no_quantize_fp32_tables", i_f)):
+        out[name] = {"recall_at_R": [float((idx[:, :R] == true_nn[:, None]).any(1).float().mean()) for R in Rs]}
+    # dot products: approximate (dequantized) vs true on a sample of pairs
+    ad, bd = quant[bolt.METRIC_DOT]
+    ld = bolt.build_luts(Q[:20], C, bolt.METRIC_DOT, ad, bd)
+    approx = bolt.dequantize(bolt.scan_dot(codes, n, M, ld), ad, bd)[:, :200_000].double()
+    true = Q[:20].double() @ Xd[:200_000].double().T
+    a_c, t_c = approx - approx.mean(), true - true.mean()
+    out["dot_correlation"] = float((a_c * t_c).sum() / (a_c.norm() * t_c.norm()))
+    del sf
+    torch.cuda.empty_cache()
+    return out
 
 
 def large_n_scan(codes, C, quant, hbm_peak, peak_kind):
@@ -647,6 +692,7 @@ def run_bolt(args, world, rank, local):
     if rank == 0 and not args.no_aux:
         del step
         torch.cuda.empty_cache()
+        line["accuracy_mixture_1m"] = accuracy_report(Xd, C, quant)
         codes50 = build_50m(C)
         line["large_n_scan"] = large_n_scan(codes50, C, quant, hbm_peak, peak_kind)
         line["serving"] = serving(codes50, C, quant)
@@ -700,6 +746,11 @@ def run_only(args):
 
     torch.cuda.set_device(0)
     bolt.lib()
+    if args.only == "accuracy":
+        cfg = workload(8)
+        X, Q, Xd, Qd, C, quant = prepare(cfg, 0)
+        print(json.dumps(accuracy_report(Xd, C, quant)), flush=True)
+        return
     if args.only == "large50m":
         cfg = workload(8)
         X, Q, Xd, Qd, C, quant = prepare(cfg, 0)

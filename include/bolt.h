@@ -124,6 +124,15 @@ int bolt_scan_l2(const uint8_t *codes, int64_t n, int32_t M,
 int bolt_scan_dot(const uint8_t *codes, int64_t n, int32_t M,
                   const uint8_t *luts, int64_t nq, uint16_t *sums, void *stream);
 
+/* "Bolt No Quantize" (the Sec. 4.2 ablation that skips the 8-bit tables):
+ * out[q][i] = sum over m = 0..M-1 of luts_f32[q][m][code_m(x_i)], summed in
+ * codebook order from 0.0f with one fp32 add (round to nearest) per
+ * codebook.  luts_f32: nq x M x 16 fp32 (the `luts_f32` output of
+ * bolt_build_luts); out: nq x n fp32.  Device pointers, codes 16-byte
+ * aligned. */
+int bolt_scan_float(const uint8_t *codes, int64_t n, int32_t M, const float *luts_f32,
+                    int64_t nq, float *out, void *stream);
+
 /* ---------------------------------------------------------------- top-k
  * Fused scan + exact top-k (nearest neighbours for L2, maximum inner product
  * for dot; Sec. 1.2 and Sec. 4.5 use these searches).  out_sums: nq x k

@@ -42,6 +42,7 @@ _SIGS = {
                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_scan_l2": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_scan_dot": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_scan_float": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_topk_workspace_bytes": ([C.c_int64, C.c_int32, C.c_int64, C.c_int32], C.c_int64),
     "bolt_topk": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
                    C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
@@ -207,6 +208,18 @@ def scan_l2(codes, n, M, luts, out=None, stream=None):
 
 def scan_dot(codes, n, M, luts, out=None, stream=None):
     return _scan(lib().bolt_scan_dot, codes, n, M, luts, out, stream)
+
+
+def scan_float(codes, n, M, luts_f32, out=None, stream=None):
+    """fp32 scan over fp32 tables ("Bolt No Quantize"): (nq, n) float32."""
+    torch = _torch()
+    _dev(codes, torch.uint8, "codes")
+    _dev(luts_f32, torch.float32, "luts_f32")
+    nq = luts_f32.shape[0]
+    if out is None:
+        out = torch.empty((nq, n), dtype=torch.float32, device=luts_f32.device)
+    _check(lib().bolt_scan_float(_ptr(codes), n, M, _ptr(luts_f32), nq, _ptr(out), _stream(stream)))
+    return out
 
 
 def topk_workspace_bytes(n, M, nq, k):

@@ -52,6 +52,47 @@ static int launch_scan_sums(const uint8_t *codes, int64_t n, int32_t M, const ui
     return check_launch("scan_sums_kernel");
 }
 
+// ------------------------------------------------------------------ float tables
+// "Bolt No Quantize" (Sec. 4.2 ablation): the same scan over the fp32 tables
+// D, summed in codebook order from 0 with one fp32 add per codebook.  One CTA
+// per (query, range of blocks); the query's M x 16 table sits in shared
+// memory, each lane looks up its 8 vectors' entries per code word.
+constexpr int kFloatThreads = 256;
+
+__global__ void __launch_bounds__(kFloatThreads) scan_float_kernel(const uint32_t *__restrict__ codes, int64_t n,
+                                                                  int32_t M, const float *__restrict__ D,
+                                                                  float *__restrict__ out, int64_t blocks_per_cta) {
+    extern __shared__ float dtab[];  // [M][16]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t q = blockIdx.y;
+    for (int i = tid; i < M * kK; i += kFloatThreads) dtab[i] = __ldg(D + q * M * kK + i);
+    __syncthreads();
+    const int64_t nb = num_blocks(n);
+    const int64_t b0 = (int64_t)blockIdx.x * blocks_per_cta;
+    const int64_t b1 = min(nb, b0 + blocks_per_cta);
+    for (int64_t b = b0 + warp; b < b1; b += kFloatThreads / 32) {
+        const uint32_t *row = codes + b * M * kRowWords + lane;
+        float acc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = 0.0f;
+#pragma unroll 4
+        for (int m = 0; m < M; ++m) {
+            const uint32_t W = __ldg(row + (int64_t)m * kRowWords);
+            const float *t = dtab + m * kK;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[i] = __fadd_rn(acc[i], t[(W >> (4 * i)) & 15u]);
+        }
+        const int64_t v0 = b * kBlockVecs + 8 * lane;
+        float *dst = out + q * n + v0;
+        if (v0 + 8 <= n && aligned(dst, 16)) {
+            reinterpret_cast<float4 *>(dst)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            reinterpret_cast<float4 *>(dst)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        } else {
+            for (int i = 0; i < 8 && v0 + i < n; ++i) dst[i] = acc[i];
+        }
+    }
+}
+
 static int check_scan_args(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq,
                            const void *out) {
     int rc = check_nm(n, M);
@@ -81,6 +122,32 @@ int bolt_scan_dot(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *lut
     int rc = bolt::check_scan_args(codes, n, M, luts, nq, sums);
     if (rc) return rc;
     return bolt::launch_scan_sums(codes, n, M, luts, nq, sums, (cudaStream_t)stream);
+}
+
+int bolt_scan_float(const uint8_t *codes, int64_t n, int32_t M, const float *luts_f32, int64_t nq, float *out,
+                    void *stream) {
+    bolt::clear_error();
+    int rc = bolt::check_nm(n, M);
+    if (rc) return rc;
+    BOLT_REQUIRE(nq >= 0, BOLT_EINVAL, "nq=%lld < 0", (long long)nq);
+    if (n == 0 || nq == 0) return BOLT_OK;
+    BOLT_REQUIRE(codes && luts_f32 && out, BOLT_EINVAL, "null pointer");
+    BOLT_REQUIRE(bolt::aligned(codes, 16) && bolt::aligned(luts_f32, 4), BOLT_EINVAL,
+                 "codes must be 16-byte aligned");
+    BOLT_REQUIRE(nq <= 65535, BOLT_EUNSUPPORTED, "nq=%lld > 65535 per call", (long long)nq);
+    const int64_t nb = bolt::num_blocks(n);
+    int64_t gx = (int64_t)(bolt::device_sm_count() > 0 ? bolt::device_sm_count() : 1) * 4;
+    gx = (gx + nq - 1) / nq;
+    if (gx > nb) gx = nb;
+    if (gx < 1) gx = 1;
+    const int64_t bpc = (nb + gx - 1) / gx;
+    gx = (nb + bpc - 1) / bpc;
+    const size_t smem = (size_t)M * bolt::kK * 4;
+    rc = bolt::ensure_smem((const void *)bolt::scan_float_kernel, smem);
+    if (rc) return rc;
+    bolt::scan_float_kernel<<<dim3((unsigned)gx, (unsigned)nq), bolt::kFloatThreads, smem, (cudaStream_t)stream>>>(
+        reinterpret_cast<const uint32_t *>(codes), n, M, luts_f32, out, bpc);
+    return bolt::check_launch("scan_float_kernel");
 }
 
 }  // extern "C"

@@ -161,6 +161,19 @@ def test_scan_sums_bitexact(torch_cuda, n, M):
         np.testing.assert_array_equal(got.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("n,J,M", [(10_000, 32, 8), (1_037, 128, 16), (70_001, 64, 32), (300, 64, 64), (257, 16, 1)])
+def test_scan_float_bitexact(torch_cuda, n, J, M):
+    """Bolt No Quantize: fp32 sums over the fp32 tables, bit-exact against
+    the oracle's sequential sum in codebook order."""
+    torch = torch_cuda
+    X, Q, C_ = problem(n, J, M, 6, "mixture", nq=9)
+    for metric in (bolt.METRIC_L2, bolt.METRIC_DOT):
+        codes = oracle.encode(X, C_)
+        D = oracle.lut_f32(Q, C_, metric)
+        got = bolt.scan_float(bolt.pack_codes(dev(torch, codes)), n, M, dev(torch, D))
+        np.testing.assert_array_equal(got.cpu().numpy(), oracle.scan_float(codes, D))
+
+
 def test_scan_extreme_tables(torch_cuda):
     """All-255 tables at M = 256 reach the largest sum 65280; all-zero give 0."""
     torch = torch_cuda
