@@ -53,6 +53,9 @@ extern "C" {
 
 #define BOLT_METRIC_L2 0  /* delta = squared difference, f = sqrt (Sec. 1.1) */
 #define BOLT_METRIC_DOT 1 /* delta = product, f = identity (Sec. 1.1) */
+#define BOLT_METRIC_L1 2  /* delta = absolute difference, f = identity: the L_p family of
+                             Sec. 1.1 with p = 1 (f = r^(1/p) is monotone, so top-k ranks
+                             by the sum, ascending, as for L2) */
 
 #define BOLT_PREC_FP32 0         /* canonical fp32 encoder */
 #define BOLT_PREC_BF16_RECHECK 1 /* tensor-core bf16 scores + fp32 re-check */

@@ -24,6 +24,7 @@ from . import build as _build
 
 METRIC_L2 = 0
 METRIC_DOT = 1
+METRIC_L1 = 2
 K = 16
 ALPHAS = (0.0, 0.001, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1)
 

@@ -53,7 +53,9 @@
 #define BO_EUNSUPPORTED 2
 #define BO_ENOMEM 3
 
-enum { BO_METRIC_L2 = 0, BO_METRIC_DOT = 1 };
+/* L1: delta = |q_j - x_j| (the L_p family of Sec. 1.1 with p = 1; f(r) = r
+ * is monotone, so nearest neighbours rank by the sum itself, ascending). */
+enum { BO_METRIC_L2 = 0, BO_METRIC_DOT = 1, BO_METRIC_L1 = 2 };
 
 static int check_shape(int64_t n, int32_t J, int32_t M) {
     if (n < 0 || J <= 0 || M <= 0) return BO_EINVAL;
@@ -217,7 +219,7 @@ int bo_lut_f32(const float *Q, int64_t nq, int32_t J, int32_t M, const float *C,
                int32_t metric, float *D) {
     int rc = check_shape(nq, J, M);
     if (rc) return rc;
-    if (metric != BO_METRIC_L2 && metric != BO_METRIC_DOT) return BO_EINVAL;
+    if (metric != BO_METRIC_L2 && metric != BO_METRIC_DOT && metric != BO_METRIC_L1) return BO_EINVAL;
     const int s = J / M;
     for (int64_t q = 0; q < nq; q++)
         for (int m = 0; m < M; m++)
@@ -230,6 +232,8 @@ int bo_lut_f32(const float *Q, int64_t nq, int32_t J, int32_t M, const float *C,
                         float t = x[j] - c[j];
                         acc = fmaf(t, t, acc);
                     }
+                } else if (metric == BO_METRIC_L1) {
+                    for (int j = 0; j < s; j++) acc = acc + fabsf(x[j] - c[j]);
                 } else {
                     for (int j = 0; j < s; j++) acc = fmaf(x[j], c[j], acc);
                 }
@@ -243,7 +247,7 @@ int bo_lut_f64(const float *Q, int64_t nq, int32_t J, int32_t M, const float *C,
                int32_t metric, double *D) {
     int rc = check_shape(nq, J, M);
     if (rc) return rc;
-    if (metric != BO_METRIC_L2 && metric != BO_METRIC_DOT) return BO_EINVAL;
+    if (metric != BO_METRIC_L2 && metric != BO_METRIC_DOT && metric != BO_METRIC_L1) return BO_EINVAL;
     const int s = J / M;
     for (int64_t q = 0; q < nq; q++)
         for (int m = 0; m < M; m++)
@@ -255,6 +259,8 @@ int bo_lut_f64(const float *Q, int64_t nq, int32_t J, int32_t M, const float *C,
                     if (metric == BO_METRIC_L2) {
                         double t = (double)x[j] - (double)c[j];
                         acc = acc + t * t;
+                    } else if (metric == BO_METRIC_L1) {
+                        acc = acc + fabs((double)x[j] - (double)c[j]);
                     } else {
                         acc = acc + (double)x[j] * (double)c[j];
                     }
@@ -427,14 +433,14 @@ int bo_scan_float(const uint8_t *codes, int64_t n, int32_t M, const float *D,
  * Nearest neighbours (smallest L2) / maximum inner product (largest dot),
  * Sec. 1.2 and Sec. 4.5.  Keeps a sorted list of the k best seen so far. */
 static int better(int32_t metric, uint16_t s1, int64_t i1, uint16_t s2, int64_t i2) {
-    if (s1 != s2) return metric == BO_METRIC_L2 ? s1 < s2 : s1 > s2;
+    if (s1 != s2) return metric == BO_METRIC_DOT ? s1 > s2 : s1 < s2;
     return i1 < i2;
 }
 
 int bo_topk(const uint16_t *sums, int64_t n, int64_t nq, int32_t k, int32_t metric,
             uint16_t *out_sums, int64_t *out_idx) {
     if (n < 0 || nq < 0 || k <= 0) return BO_EINVAL;
-    if (metric != BO_METRIC_L2 && metric != BO_METRIC_DOT) return BO_EINVAL;
+    if (metric != BO_METRIC_L2 && metric != BO_METRIC_DOT && metric != BO_METRIC_L1) return BO_EINVAL;
     for (int64_t q = 0; q < nq; q++) {
         uint16_t *bs = out_sums + q * k;
         int64_t *bi = out_idx + q * k;

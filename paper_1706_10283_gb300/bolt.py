@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbolt.so")
 
 OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, ETIMEOUT = range(6)
-METRIC_L2, METRIC_DOT = 0, 1
+METRIC_L2, METRIC_DOT, METRIC_L1 = 0, 1, 2
 PREC_FP32, PREC_BF16_RECHECK = 0, 1
 K = 16
 BLOCK = 256

@@ -268,7 +268,8 @@ int bolt_fit_quantizer(const float *Qtrain, int64_t nqt, int32_t J, int32_t M, c
     int rc = bolt::check_jm(J, M);
     if (rc) return rc;
     BOLT_REQUIRE(nqt >= 1, BOLT_EINVAL, "need at least one training query");
-    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT, BOLT_EINVAL, "bad metric %d", metric);
+    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT || metric == BOLT_METRIC_L1, BOLT_EINVAL,
+                 "bad metric %d", metric);
     BOLT_REQUIRE(Qtrain && centroids && a_host && b_host, BOLT_EINVAL, "null pointer");
     return bolt::fit_quantizer_impl(Qtrain, nqt, J, M, centroids, metric, a_host, b_host, alpha_idx_host,
                                     (cudaStream_t)stream);

@@ -5,7 +5,8 @@
 namespace bolt {
 
 // Canonical fp32 table entry.  L2: acc = fma(t, t, acc), t = q_j - c_j;
-// dot: acc = fma(q_j, c_j, acc); dims in order, starting from 0.
+// dot: acc = fma(q_j, c_j, acc); L1: acc = acc + |q_j - c_j|; dims in order,
+// starting from 0.
 __device__ __forceinline__ float lut_entry(const float *__restrict__ q, const float *__restrict__ c, int s,
                                            int metric) {
     float acc = 0.0f;
@@ -14,6 +15,8 @@ __device__ __forceinline__ float lut_entry(const float *__restrict__ q, const fl
             const float t = __fsub_rn(q[j], c[j]);
             acc = __fmaf_rn(t, t, acc);
         }
+    } else if (metric == BOLT_METRIC_L1) {
+        for (int j = 0; j < s; ++j) acc = __fadd_rn(acc, fabsf(__fsub_rn(q[j], c[j])));
     } else {
         for (int j = 0; j < s; ++j) acc = __fmaf_rn(q[j], c[j], acc);
     }
@@ -74,7 +77,8 @@ extern "C" int bolt_build_luts(const float *Q, int64_t nq, int32_t J, int32_t M,
     int rc = bolt::check_jm(J, M);
     if (rc) return rc;
     BOLT_REQUIRE(nq >= 0, BOLT_EINVAL, "nq=%lld < 0", (long long)nq);
-    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT, BOLT_EINVAL, "bad metric %d", metric);
+    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT || metric == BOLT_METRIC_L1, BOLT_EINVAL,
+                 "bad metric %d", metric);
     BOLT_REQUIRE(nq == 0 || (Q && centroids && luts), BOLT_EINVAL, "null pointer");
     bolt::QuantParams qp;
     rc = bolt::make_quant_params(a, b_host, M, &qp);

@@ -908,7 +908,8 @@ int bolt_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, i
     int rc = bolt::check_nm(n, M);
     if (rc) return rc;
     BOLT_REQUIRE(nq >= 0, BOLT_EINVAL, "nq=%lld < 0", (long long)nq);
-    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT, BOLT_EINVAL, "bad metric %d", metric);
+    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT || metric == BOLT_METRIC_L1, BOLT_EINVAL,
+                 "bad metric %d", metric);
     bolt::TopkPlan plan;
     rc = bolt::plan_topk(n, M, k, nq, &plan);
     if (rc) return rc;
@@ -976,7 +977,8 @@ extern "C" int bolt_topk_noalloc(const uint8_t *codes, int64_t n, int32_t M, con
     int rc = bolt::check_nm(n, M);
     if (rc) return rc;
     BOLT_REQUIRE(nq >= 0, BOLT_EINVAL, "nq=%lld < 0", (long long)nq);
-    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT, BOLT_EINVAL, "bad metric %d", metric);
+    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT || metric == BOLT_METRIC_L1, BOLT_EINVAL,
+                 "bad metric %d", metric);
     bolt::TopkPlan plan;
     rc = bolt::plan_topk(n, M, k, nq, &plan);
     if (rc) return rc;

@@ -129,7 +129,7 @@ def test_encode_tensor_core_near_ties(torch_cuda, scale):
 
 
 # ------------------------------------------------------------------ LUT
-@pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
+@pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT, bolt.METRIC_L1])
 @pytest.mark.parametrize("n,J,M,kind", SHAPES[:5])
 def test_luts_bitexact(torch_cuda, metric, n, J, M, kind):
     torch = torch_cuda
@@ -142,7 +142,7 @@ def test_luts_bitexact(torch_cuda, metric, n, J, M, kind):
     np.testing.assert_array_equal(luts.cpu().numpy(), oracle.quantize(D, a, b))
     D64 = oracle.lut_f64(Q, C_, metric)
     # 1e-5 relative to the magnitude of the terms summed (|q||c| scale)
-    scale = np.abs(D64) if metric == bolt.METRIC_L2 else (
+    scale = np.abs(D64) if metric != bolt.METRIC_DOT else (
         np.abs(Q).reshape(37, M, 1, -1) * np.abs(C_)[None]).sum(-1)
     assert np.all(np.abs(f32.cpu().numpy() - D64) <= 1e-5 * np.maximum(scale, 1e-30))
 
@@ -221,6 +221,16 @@ def test_topk_large_database_paths(torch_cuda, metric, hi, nq):
     codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
     luts = rng.integers(0, hi, (nq, M, 16)).astype(np.uint8)
     check_topk(torch_cuda, codes, luts, k, metric)
+
+
+@pytest.mark.parametrize("n,M,k,nq", [(1000, 8, 10, 1), (100_003, 16, 100, 2), (3_000_000, 16, 50, 5)])
+def test_topk_l1_tables_rank_ascending(torch_cuda, n, M, k, nq):
+    """L1 tables (the L_p family with p = 1): top-k ranks by ascending sum,
+    through every size class (shared-memory, streaming, multi-query)."""
+    rng = np.random.default_rng(n + M + k)
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+    luts = rng.integers(0, 256, (nq, M, 16)).astype(np.uint8)
+    check_topk(torch_cuda, codes, luts, k, bolt.METRIC_L1)
 
 
 @pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])

@@ -154,7 +154,7 @@ def test_kmeans_empty_cluster_keeps_centroid():
 
 
 # ------------------------------------------------------------------ LUT g
-@pytest.mark.parametrize("metric", [oracle.METRIC_L2, oracle.METRIC_DOT])
+@pytest.mark.parametrize("metric", [oracle.METRIC_L2, oracle.METRIC_DOT, oracle.METRIC_L1])
 def test_lut_decomposition_equals_distance_to_reconstruction(metric):
     """Sec. 3.1: the sum over subspaces of the table entries picked by the
     codes equals the distance between q and the reconstruction x_hat."""
@@ -168,11 +168,13 @@ def test_lut_decomposition_equals_distance_to_reconstruction(metric):
     got = D[:, np.arange(8)[None, :], codes].sum(axis=2)  # (nq, n)
     if metric == oracle.METRIC_L2:
         ref = cdist(Q.astype(np.float64), xh, "sqeuclidean")
+    elif metric == oracle.METRIC_L1:
+        ref = cdist(Q.astype(np.float64), xh, "cityblock")
     else:
         ref = Q.astype(np.float64) @ xh.T
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
     D32 = oracle.lut_f32(Q, C, metric)
-    scale = np.abs(Q).max() * np.abs(C).max() * 4 + (D if metric == 0 else 0)
+    scale = np.abs(Q).max() * np.abs(C).max() * 4 + (D if metric != oracle.METRIC_DOT else 0)
     assert np.all(np.abs(D32 - D) <= 1e-5 * np.maximum(1.0, np.abs(D)) * 4 + 1e-6 * scale)
 
 
@@ -182,10 +184,15 @@ def test_lut_matches_cdist_per_subspace():
     Q = rng.standard_normal((5, 32)).astype(np.float32)
     D = oracle.lut_f64(Q, C, oracle.METRIC_L2)
     Dd = oracle.lut_f64(Q, C, oracle.METRIC_DOT)
+    D1 = oracle.lut_f64(Q, C, oracle.METRIC_L1)
+    D1f = oracle.lut_f32(Q, C, oracle.METRIC_L1)
     for m in range(4):
         q = Q[:, 8 * m:8 * m + 8].astype(np.float64)
         np.testing.assert_allclose(D[:, m, :], cdist(q, C[m].astype(np.float64), "sqeuclidean"), rtol=1e-13)
         np.testing.assert_allclose(Dd[:, m, :], q @ C[m].astype(np.float64).T, rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(D1[:, m, :], cdist(q, C[m].astype(np.float64), "cityblock"), rtol=1e-13)
+        # fp32 entry: 8 fp32 subtractions and adds, each within half an ulp
+        np.testing.assert_allclose(D1f[:, m, :], D1[:, m, :], rtol=8 * 2.0 ** -23)
 
 
 def test_lut_exact_when_x_is_made_of_centroids():
@@ -321,7 +328,7 @@ def test_scan_float_is_bolt_no_quantize_sum():
 
 
 # ------------------------------------------------------------------ top-k
-@pytest.mark.parametrize("metric", [oracle.METRIC_L2, oracle.METRIC_DOT])
+@pytest.mark.parametrize("metric", [oracle.METRIC_L2, oracle.METRIC_DOT, oracle.METRIC_L1])
 def test_topk_matches_lexsort(metric):
     rng = np.random.default_rng(16)
     sums = rng.integers(0, 40, (3, 5000)).astype(np.uint16)  # many ties
@@ -329,7 +336,7 @@ def test_topk_matches_lexsort(metric):
     got_s, got_i = oracle.topk(sums, k, metric)
     for q in range(3):
         idx = np.arange(5000)
-        key = sums[q].astype(np.int64) if metric == oracle.METRIC_L2 else -sums[q].astype(np.int64)
+        key = -sums[q].astype(np.int64) if metric == oracle.METRIC_DOT else sums[q].astype(np.int64)
         order = np.lexsort((idx, key))[:k]
         np.testing.assert_array_equal(got_i[q], order)
         np.testing.assert_array_equal(got_s[q], sums[q][order])
