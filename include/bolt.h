@@ -252,6 +252,29 @@ int bolt_topk_merge(const uint16_t *sums, const int64_t *idx, const int64_t *off
                     int32_t nshard, int64_t nq, int32_t k, int32_t M, int32_t metric,
                     uint16_t *out_sums, int64_t *out_idx, void *stream);
 
+/* ---------------------------------------------------------------- online changes
+ * Databases that change while in use (Sec. 1.3: vectors are added and
+ * changed online).  bolt_write_codes writes the codes of `count` vectors --
+ * rowmajor: count x M bytes, each 0..15 (e.g. bolt_unpack_codes of a
+ * bolt_encode result) -- into rows[i] of a blocked code array with room for
+ * n_cap vectors (bolt_codes_bytes(n_cap, M) bytes).  rows: count distinct
+ * int64 (device).  A row outside [0, n_cap) or a code above 15 is not
+ * written and the call returns BOLT_EINVAL.  Synchronizes `stream` (to
+ * report bad rows).  Calls that scan the array must not overlap it. */
+int bolt_write_codes(const uint8_t *rowmajor, int64_t count, int32_t M, const int64_t *rows,
+                     uint8_t *blocked, int64_t n_cap, void *stream);
+
+/* Drop deleted vectors from top-k lists: for each of nq lists (in_sums /
+ * in_idx: nq x k_in, best first, as from bolt_topk), the first k_out
+ * entries whose index i is live (bit i of dead_bits clear; indices at or
+ * past n_bits are live), in list order, padded with index -1 and sum 0.
+ * If at most D rows are dead, the top k_out of the live rows is the
+ * filtered top (k_out + D) of all rows.  A list holding index -2 (a failed
+ * wait) comes out all -2.  Device pointers. */
+int bolt_topk_filter(const uint16_t *in_sums, const int64_t *in_idx, int64_t nq, int32_t k_in,
+                     const uint32_t *dead_bits, int64_t n_bits, int32_t k_out, uint16_t *out_sums,
+                     int64_t *out_idx, void *stream);
+
 /* ---------------------------------------------------------------- dequantize
  * Sec. 3.2: the per-table reconstructions beta_m/a + b_m sum to
  * S * (1/a) + sum_m b_m.  Host helper (fp64, no GPU): inv_a =

@@ -58,6 +58,9 @@ _SIGS = {
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_topk_merge": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.c_int32,
                          C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_write_codes": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
+    "bolt_topk_filter": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_int32,
+                          C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_batch_plan_bytes": ([C.c_void_p, C.c_int32], C.c_int64),
     "bolt_batch_plan": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "bolt_scan_batched": ([C.c_void_p, C.c_void_p], C.c_int),
@@ -262,6 +265,32 @@ def topk_merge(sums, idx, offsets, M, metric, out_sums=None, out_idx=None, strea
     _check(lib().bolt_topk_merge(_ptr(sums), _ptr(idx), _ptr(offsets), nshard, nq, k, M, metric, _ptr(out_sums),
                                  _ptr(out_idx), _stream(stream)))
     return out_sums, out_idx
+
+
+def write_codes(rowmajor, rows, blocked, n_cap, stream=None):
+    """Write row-major codes (count, M) uint8 into rows (count,) int64 of a
+    blocked code array with room for n_cap vectors."""
+    torch = _torch()
+    _dev(rowmajor, torch.uint8, "rowmajor")
+    _dev(rows, torch.int64, "rows")
+    _dev(blocked, torch.uint8, "blocked")
+    count, M = rowmajor.shape
+    _check(lib().bolt_write_codes(_ptr(rowmajor), count, M, _ptr(rows), _ptr(blocked), n_cap, _stream(stream)))
+
+
+def topk_filter(sums, idx, dead_bits, n_bits, k_out, stream=None):
+    """Keep the first k_out live entries of each top-k list (dead_bits: int32
+    tensor viewed as a bitmap of dead rows)."""
+    torch = _torch()
+    _dev(sums, torch.uint16, "sums")
+    _dev(idx, torch.int64, "idx")
+    _dev(dead_bits, torch.int32, "dead_bits")
+    nq, k_in = idx.shape
+    out_s = torch.empty((nq, k_out), dtype=torch.uint16, device=idx.device)
+    out_i = torch.empty((nq, k_out), dtype=torch.int64, device=idx.device)
+    _check(lib().bolt_topk_filter(_ptr(sums), _ptr(idx), nq, k_in, _ptr(dead_bits), n_bits, k_out, _ptr(out_s),
+                                  _ptr(out_i), _stream(stream)))
+    return out_s, out_i
 
 
 # ------------------------------------------------------------------ dequantize / matmul

@@ -130,18 +130,39 @@ class BatchPolicy:
 
 
 class Collection:
-    """A resident encoded database: codes (blocked, device), codebooks and
-    per-metric quantizers (a, b)."""
+    """A resident encoded database: codes (blocked, device, room for
+    `capacity` vectors), codebooks and per-metric quantizers (a, b).
 
-    def __init__(self, name, codes, n, M, centroids, quant):
+    Rows [0, n) are in use; deleted rows are marked in a device bitmap
+    (`dead`), kept in `free` for reuse by later inserts, and dropped from
+    search results (top-(k + n_dead) followed by bolt_topk_filter, exact
+    because at most n_dead dead rows can rank above a live one)."""
+
+    def __init__(self, name, codes, n, M, centroids, quant, capacity=None):
+        import torch
+
         self.name = name
         self.codes = codes
         self.n = int(n)
         self.M = int(M)
+        self.capacity = int(capacity if capacity is not None else n)
+        if codes.numel() < bolt.codes_bytes(self.capacity, self.M):
+            raise AdmissionError("collection %r: codes hold fewer than %d vectors" % (name, self.capacity))
         self.C = centroids
         self.J = int(centroids.shape[0] * centroids.shape[2])
         self.quant = {m: (float(a), np.asarray(b, np.float32)) for m, (a, b) in quant.items()}
-        self.nbytes = int(codes.numel() + centroids.numel() * 4)
+        self.dead_host = np.zeros((self.capacity + 31) // 32, np.uint32)
+        self.dead = torch.zeros(len(self.dead_host), dtype=torch.int32, device=codes.device)
+        self.free = []
+        self.n_dead = 0
+        self.nbytes = int(codes.numel() + centroids.numel() * 4 + self.dead.numel() * 4)
+
+    def is_dead(self, i):
+        return bool((self.dead_host[i >> 5] >> np.uint32(i & 31)) & np.uint32(1))
+
+    def _set_dead(self, i, v):
+        w, b = i >> 5, np.uint32(1 << (i & 31))
+        self.dead_host[w] = (self.dead_host[w] | b) if v else (self.dead_host[w] & ~b)
 
 
 def batch_bytes(coll, kind, nq, k):
@@ -149,7 +170,9 @@ def batch_bytes(coll, kind, nq, k):
     q = nq * coll.J * 4
     if kind == MATMUL:
         return q + nq * coll.M * 16 + nq * coll.n * 4
-    return (q + nq * coll.M * 16 + bolt.topk_workspace_bytes(coll.n, coll.M, nq, k) + nq * k * (2 + 8 + 4))
+    kr = k + coll.n_dead
+    return (q + nq * coll.M * 16 + bolt.topk_workspace_bytes(coll.n, coll.M, nq, kr) + nq * kr * (2 + 8) * 2 +
+            nq * k * 4)
 
 
 class _Slot:
@@ -190,10 +213,10 @@ class Server:
         self.resident = 0  # bytes of admitted collections
 
     # -------------------------------------------------------------- collections
-    def add_collection(self, name, codes, n, M, centroids, quant):
+    def add_collection(self, name, codes, n, M, centroids, quant, capacity=None):
         if name in self.collections:
             raise AdmissionError("collection %r already resident" % name)
-        c = Collection(name, codes, n, M, centroids, quant)
+        c = Collection(name, codes, n, M, centroids, quant, capacity)
         if not self.budget.reserve(c.nbytes):
             raise AdmissionError("collection %r (%d bytes) does not fit the HBM budget (%d of %d bytes used)" %
                                  (name, c.nbytes, self.budget.used, self.budget.total))
@@ -209,6 +232,75 @@ class Server:
         self.budget.release(c.nbytes)
         self.resident -= c.nbytes
 
+    # -------------------------------------------------------------- online changes
+    def _quiesce(self, name):
+        """Wait for the batches in flight on collection `name` (their results
+        are retired by the next poll)."""
+        for s in self.slots:
+            if s.busy and s.reqs and s.reqs[0][0].collection == name:
+                s.event.synchronize()
+
+    def _encode_rows(self, c, X):
+        torch = self.torch
+        Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(self.device)
+        if Xd.ndim != 2 or Xd.shape[1] != c.J:
+            raise ValueError("vectors must be (count, %d)" % c.J)
+        blocked = bolt.encode(Xd, c.C)
+        return bolt.unpack_codes(blocked, Xd.shape[0], c.M)
+
+    def insert(self, name, X):
+        """Encode vectors X (count, J) and store them, reusing deleted rows
+        first; returns their row ids.  Waits for the collection's batches in
+        flight."""
+        torch = self.torch
+        c = self.collections[name]
+        count = int(np.asarray(X).shape[0])
+        reuse = min(count, len(c.free))
+        fresh = count - reuse
+        if c.n + fresh > c.capacity:
+            raise AdmissionError("collection %r: %d rows free, %d needed" % (name, c.capacity - c.n + len(c.free),
+                                                                            count))
+        self._quiesce(name)
+        rows = np.array(c.free[:reuse] + list(range(c.n, c.n + fresh)), np.int64)
+        del c.free[:reuse]
+        rowcodes = self._encode_rows(c, X)
+        bolt.write_codes(rowcodes, torch.from_numpy(rows).to(self.device), c.codes, c.capacity)
+        for i in rows[:reuse]:
+            c._set_dead(int(i), False)
+        c.n_dead -= reuse
+        c.n += fresh
+        if reuse:
+            c.dead.copy_(torch.from_numpy(c.dead_host.view(np.int32)))
+            torch.cuda.current_stream().synchronize()  # later batches run on other streams
+        return rows
+
+    def update(self, name, ids, X):
+        """Replace the vectors of live rows `ids` by X (re-encoded)."""
+        torch = self.torch
+        c = self.collections[name]
+        ids = np.asarray(ids, np.int64)
+        if len(set(ids.tolist())) != len(ids) or any(i < 0 or i >= c.n or c.is_dead(int(i)) for i in ids):
+            raise ValueError("update needs distinct live row ids")
+        self._quiesce(name)
+        bolt.write_codes(self._encode_rows(c, X), torch.from_numpy(ids).to(self.device), c.codes, c.capacity)
+
+    def delete(self, name, ids):
+        """Mark rows `ids` deleted: searches no longer return them and
+        inserts reuse them."""
+        torch = self.torch
+        c = self.collections[name]
+        ids = np.asarray(ids, np.int64)
+        if any(i < 0 or i >= c.n for i in ids):
+            raise ValueError("row id out of range")
+        self._quiesce(name)
+        for i in ids.tolist():
+            if not c.is_dead(i):
+                c._set_dead(i, True)
+                c.free.append(i)
+                c.n_dead += 1
+        c.dead.copy_(torch.from_numpy(c.dead_host.view(np.int32)))
+        torch.cuda.current_stream().synchronize()  # later batches run on other streams
+
     # -------------------------------------------------------------- requests
     def submit(self, req):
         c = self.collections.get(req.collection)
@@ -218,6 +310,9 @@ class Server:
             raise ValueError("request %r: queries must be (nq, %d)" % (req.rid, c.J))
         if req.kind == SEARCH and not 1 <= req.k <= 1024:
             raise ValueError("request %r: k=%d outside [1, 1024]" % (req.rid, req.k))
+        if req.kind == SEARCH and req.k + c.n_dead > 1024:
+            raise AdmissionError("request %r: k + %d deleted rows exceeds 1024; insert vectors to reuse them"
+                                 % (req.rid, c.n_dead))
         if batch_bytes(c, req.kind, req.nq, req.k) + self.resident > self.budget.total:
             raise AdmissionError("request %r can never fit the HBM budget" % req.rid)
         self.queue.append(req)
@@ -305,9 +400,12 @@ class Server:
                 self.launches += 1
             else:
                 luts = bolt.build_luts(Qd, c.C, head.metric, a, b, stream=s)
-                ws = torch.empty(bolt.topk_workspace_bytes(c.n, c.M, nq, kb), dtype=torch.uint8,
+                kr = kb + c.n_dead  # deleted rows are filtered out of a longer list
+                ws = torch.empty(bolt.topk_workspace_bytes(c.n, c.M, nq, kr), dtype=torch.uint8,
                                  device=self.device)
-                sums, idx = bolt.topk(c.codes, c.n, c.M, luts, kb, head.metric, workspace=ws, stream=s)
+                sums, idx = bolt.topk(c.codes, c.n, c.M, luts, kr, head.metric, workspace=ws, stream=s)
+                if c.n_dead:
+                    sums, idx = bolt.topk_filter(sums, idx, c.dead, c.capacity, kb, stream=s)
                 dist = bolt.dequantize(sums, a, b, stream=s)
                 ih = slot.pinned(torch, "idx", nq * kb, torch.int64).view(nq, kb)
                 dh = slot.pinned(torch, "dist", nq * kb, torch.float32).view(nq, kb)

@@ -110,7 +110,8 @@ def test_tight_budget_serializes_but_results_hold(torch_cuda, world):
     """A budget that fits the collections and about one batch: requests wait
     for memory, the books never exceed the budget, results are unchanged."""
     torch = torch_cuda
-    resident = sum(w["codes"].numel() + w["Cd"].numel() * 4 for w in world.values())
+    resident = sum(serve.Collection(nm, w["codes"], w["n"], w["M"], w["Cd"], w["quant"]).nbytes
+                   for nm, w in world.items())
     reqs = make_trace(6, 60, rate=5000.0)
     probe = make_server(torch, world, budget=2 << 30, slots=1)
     largest = max(serve.batch_bytes(probe.collections[r.collection], r.kind, r.nq, r.k) for r in reqs)
@@ -139,7 +140,7 @@ def test_served_search_matches_oracle(torch_cuda, world):
 def test_admission_by_budget(torch_cuda, world):
     torch = torch_cuda
     w = world["db"]
-    small = w["codes"].numel() + w["Cd"].numel() * 4
+    small = serve.Collection("db", w["codes"], w["n"], w["M"], w["Cd"], w["quant"]).nbytes
     srv = serve.Server(small + 1000, slots=1)
     srv.add_collection("db", w["codes"], w["n"], w["M"], w["Cd"], w["quant"])
     with pytest.raises(serve.AdmissionError):
