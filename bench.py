@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--graph-reps", type=int, default=0, help="also time graph replays of the launches")
     ap.add_argument("--collections", type=int, default=64, help="--only batch: first N collections")
-    ap.add_argument("--topk-streams", type=int, default=3, help="streams the step's one-query launches use")
+    ap.add_argument("--topk-streams", type=int, default=8, help="streams the step's one-query launches use")
     return ap.parse_args()
 
 

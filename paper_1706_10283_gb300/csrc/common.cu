@@ -7,6 +7,7 @@
 #include <utility>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace bolt {
 
@@ -71,6 +72,20 @@ int check_jm(int32_t J, int32_t M) {
     BOLT_REQUIRE(J % M == 0, BOLT_EUNSUPPORTED, "J=%d is not a multiple of M=%d", J, M);
     BOLT_REQUIRE(J / M <= 256, BOLT_EUNSUPPORTED, "subspace dim J/M=%d > 256 is unsupported", J / M);
     return BOLT_OK;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
 }
 
 }  // namespace bolt

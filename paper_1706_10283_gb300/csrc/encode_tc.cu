@@ -36,6 +36,7 @@
 #include <mutex>
 
 #include "encode.cuh"
+#include "tma.cuh"
 
 namespace bolt {
 
@@ -123,13 +124,6 @@ __device__ __forceinline__ uint32_t swz_off(int r, int j) {
 }
 
 // 2-D tiled TMA load of box (32 dims, 128 rows) at (x = dim, y = row).
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
 
 // Canonical fp32 distance (the encoder's definition) of subvector (r, dims
 // j0..j0+s) of a staged chunk to one centroid c (s contiguous floats).
@@ -420,22 +414,6 @@ bool encode_tc_supported(int32_t J, int32_t M) {
     return (s == 4 || s == 8 || s == 16 || s == 32) && J % kTcKC == 0;
 }
 
-// cuTensorMapEncodeTiled from the driver (looked up once through the runtime).
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static std::once_flag once;
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
-// X as a 2-D fp32 tensor {J, n} with 128 x 32 boxes and the 128-byte swizzle.
 static int make_x_map(const float *X, int64_t n, int32_t J, CUtensorMap *map) {
     auto enc = tensor_map_encoder();
     BOLT_REQUIRE(enc, BOLT_ECUDA, "cuTensorMapEncodeTiled is unavailable");

@@ -29,6 +29,7 @@
 #include "topk.cuh"
 
 #include "scan_core.cuh"
+#include "tma.cuh"
 
 namespace bolt {
 
@@ -38,6 +39,7 @@ constexpr int kSmallChunk = 8;  // blocks per bulk copy
 constexpr uint64_t kSmallWait = 1000000000ull;  // 1 s bound on every mbarrier wait
 constexpr int kSmallMiscWords = 64;
 constexpr uint32_t kPad = 0xFFFFu;  // s' of padding vectors (every real s' <= 255 * 256)
+constexpr int kSmallPrefix = 16;     // keys per list the merge copies to shared memory
 
 // Exclusive block-wide prefix sum of one value per thread (T = 512).
 // wsum: kSmallWarps + 1 words of shared scratch.  Returns the prefix and the
@@ -138,14 +140,15 @@ struct SmallWS {
     uint32_t *status;  // [nq] bit 0: a bounded wait gave up
     uint32_t *ghist;   // [nq][kBins] histogram of s' >> hshift over every CTA's kept keys
     uint32_t *cnt;     // [nq][G] entries in each CTA's list
-    uint64_t *keys;    // [nq][G * k rounded up to even] (s' << 32 | index), vector order within a list
+    uint64_t *keys;    // [nq][G][k rounded up to even] (s' << 32 | index), sorted within a list
 };
 
 template <int MT>
-__global__ void __launch_bounds__(kSmallThreads, 1)
+__global__ void __launch_bounds__(kSmallThreads, 2)
     topk_small_kernel(const uint32_t *__restrict__ codes, int64_t n, int32_t M, const uint8_t *__restrict__ luts,
                       int32_t k, int32_t metric, SmallWS ws, int nbc, int hshift,
-                      uint16_t *__restrict__ out_sums, int64_t *__restrict__ out_idx) {
+                      uint16_t *__restrict__ out_sums, int64_t *__restrict__ out_idx,
+                      const __grid_constant__ CUtensorMap lmap) {
     extern __shared__ __align__(128) uint8_t smem[];
     if (MT > 0) M = MT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -247,8 +250,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     const int64_t nvalid = min((int64_t)L, n - b0 * kBlockVecs);
     const uint32_t kk = (uint32_t)min((int64_t)k, nvalid);
     auto s_of = [&](int e) -> uint32_t { return sums_s[e]; };
-    const int64_t qstride = ((int64_t)G * k + 1) & ~(int64_t)1;  // even: 16-byte aligned per query
-    uint64_t *mine = ws.keys + q * qstride + (int64_t)cta * k;
+    const int kslot = k + (k & 1);  // even: every list starts 16-byte aligned
+    const int64_t qstride = (int64_t)G * kslot;
+    uint64_t *mine = ws.keys + q * qstride + (int64_t)cta * kslot;
     uint64_t *kept = reinterpret_cast<uint64_t *>(
         region + small_align_dev((size_t)nbc * blk_bytes + (size_t)nbc * kBlockVecs * 2, 16));
     if (!bad) {
@@ -304,13 +308,18 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     // keys gives the k-th smallest s' of the union (T2) and the number below
     // it (c2); each list then contributes a prefix: its keys below T2, and
     // its keys equal to T2 while fewer than k - c2 such keys precede them in
-    // vector order (lists are in CTA order = vector order).
-    uint32_t *cnt_s = reinterpret_cast<uint32_t *>(region);  // [G] counts, [G] lt offsets, [G] eq offsets
-    uint32_t *lt_s = cnt_s + G;
-    uint32_t *eq_s = lt_s + G;
-    uint32_t *lc_s = eq_s + G;  // [G] keys below T2 per list
-    uint64_t *all = reinterpret_cast<uint64_t *>(region + small_align_dev((size_t)G * 16, 16));
-    const uint32_t slot_bytes = (uint32_t)(((size_t)G * k * 8 + 15) & ~(size_t)15);
+    // vector order (lists are in CTA order = vector order).  The first kp
+    // keys of every list come in with one 2-D tensor copy; keys past them
+    // (long prefixes: heavy ties) are read from global memory.
+    const int kp = min(k, kSmallPrefix) + (min(k, kSmallPrefix) & 1);
+    uint32_t *cnt_s = reinterpret_cast<uint32_t *>(region);  // [G] counts; then keys below T2
+    uint32_t *lt_s = cnt_s + G;                              // [G] offsets of the keys below T2
+    uint32_t *eq_s = lt_s + G;                               // [G] offsets of the keys equal to T2
+    // [G][kp], 128-byte aligned (tensor-copy destination)
+    uint64_t *pre = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(region) + (size_t)G * 12 + 127) &
+                                                 ~uintptr_t(127));
+    uint64_t *fin = pre + (size_t)G * kp;
+    const uint64_t *lists = ws.keys + q * qstride;
     uint64_t *mbar = bars + nch;  // fresh barrier for the merge copies
     if (tid == 0) {
         mbar_init(mbar, 1);
@@ -318,8 +327,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
         // the lists and the histogram were written by other CTAs, and this
         // CTA's shared memory was last used, through the generic proxy
         asm volatile("fence.proxy.async;" ::: "memory");
-        mbar_arrive_expect_tx(mbar, slot_bytes + kBins * 4);
-        bulk_g2s(all, ws.keys + q * qstride, slot_bytes, mbar);
+        mbar_arrive_expect_tx(mbar, (uint32_t)(G * kp * 8 + kBins * 4));
+        tma_load_2d(pre, &lmap, 0, (int)(q * G), mbar);
         bulk_g2s(hist, ws.ghist + q * kBins, kBins * 4, mbar);
     }
     if (tid < G) cnt_s[tid] = __ldcg(ws.cnt + q * G + tid);
@@ -335,15 +344,21 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     uint32_t total = 0;
     small_scan(tid < G ? cnt_s[tid] : 0u, wsum, total);
     const int kout = qbad ? 0 : (int)min((uint32_t)k, total);
-    uint64_t *fin = all + (size_t)G * k;
-    fin = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(fin) + 31) & ~uintptr_t(15));
-    // first position in list c whose s' (or s' >> sh) is >= v
+    auto key_at = [&](int c, uint32_t j) -> uint64_t {
+        return j < (uint32_t)kp ? pre[(size_t)c * kp + j] : __ldcg(lists + (int64_t)c * kslot + j);
+    };
+    // first position in list c whose s' >> sh is >= v (binary search; past
+    // the copied prefix only when the prefix's last key is below v)
     auto lower = [&](int c, uint32_t v, int sh) -> uint32_t {
-        const uint64_t *lst = all + (size_t)c * k;
-        uint32_t lo = 0, hi = cnt_s[c];
+        const uint32_t len = cnt_s[c];
+        uint32_t lo = 0, hi = min(len, (uint32_t)kp);
+        if (hi == (uint32_t)kp && hi < len && ((uint32_t)(pre[(size_t)c * kp + kp - 1] >> 32) >> sh) < v) {
+            lo = hi;
+            hi = len;
+        }
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
-            if (((uint32_t)(lst[mid] >> 32) >> sh) < v) lo = mid + 1;
+            if (((uint32_t)(key_at(c, mid) >> 32) >> sh) < v) lo = mid + 1;
             else hi = mid;
         }
         return lo;
@@ -359,7 +374,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
             for (int c = warp; c < G; c += kSmallWarps) {
                 const uint32_t lo = lower(c, B2, hshift), hi = lower(c, B2 + 1, hshift);
                 for (uint32_t j = lo + lane; j < hi; j += 32)
-                    atomicAdd(&hist[(uint32_t)(all[(size_t)c * k + j] >> 32) & mask], 1u);
+                    atomicAdd(&hist[(uint32_t)(key_at(c, j) >> 32) & mask], 1u);
             }
             __syncthreads();
             uint32_t below2;
@@ -372,22 +387,21 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
         if (tid < G) {
             lt = lower(tid, T2, 0);
             eq = lower(tid, T2 + 1, 0) - lt;
-            lc_s[tid] = lt;
         }
         uint32_t t1, t2;
         const uint32_t lt_off = small_scan(lt, wsum, t1);
         const uint32_t eq_off = small_scan(eq, wsum, t2);
         if (tid < G) {
+            cnt_s[tid] = lt;  // the list's keys below T2 (its length is no longer needed)
             lt_s[tid] = lt_off;
             eq_s[tid] = eq_off;
         }
         __syncthreads();
         for (int c = warp; c < G; c += kSmallWarps) {
-            const uint64_t *lst = all + (size_t)c * k;
-            const uint32_t nlt = lc_s[c], lo = lt_s[c], eo = eq_s[c];
+            const uint32_t nlt = cnt_s[c], lo = lt_s[c], eo = eq_s[c];
             const uint32_t neq = eo < r ? min(r - eo, (c + 1 < G ? eq_s[c + 1] : t2) - eo) : 0u;
-            for (uint32_t j = lane; j < nlt; j += 32) fin[lo + j] = lst[j];
-            for (uint32_t j = lane; j < neq; j += 32) fin[c2 + eo + j] = lst[nlt + j];
+            for (uint32_t j = lane; j < nlt; j += 32) fin[lo + j] = key_at(c, j);
+            for (uint32_t j = lane; j < neq; j += 32) fin[c2 + eo + j] = key_at(c, nlt + j);
         }
         __syncthreads();
     }
@@ -445,7 +459,8 @@ bool plan_topk_small(int64_t n, int32_t M, int32_t k, int sms, TopkPlan *plan) {
     int64_t G = sms;
     if (G > nb) G = nb;
     if (G > kSmallMergeKeys / k) G = kSmallMergeKeys / k;
-    if (G < 1 || G > kSmallThreads) return false;
+    if (G > 256) G = 256;  // tensor-map box rows
+    if (G < 1) return false;
     const int64_t nbc = (nb + G - 1) / G;
     G = (nb + nbc - 1) / nbc;  // every CTA gets at least one block
     int P = 1;
@@ -453,8 +468,8 @@ bool plan_topk_small(int64_t n, int32_t M, int32_t k, int sms, TopkPlan *plan) {
     const int nch = (int)((nbc + kSmallChunk - 1) / kSmallChunk);
     const size_t scan_region = small_align((size_t)nbc * M * kRowBytes + (size_t)nbc * kBlockVecs * 2, 16) +
                                (size_t)k * 8;
-    const size_t merge_region = small_align((size_t)G * 16, 16) + small_align((size_t)G * k * 8, 16) + 32 +
-                                (size_t)2 * P * 8;
+    const size_t kp = (size_t)((k < kSmallPrefix ? k : kSmallPrefix) + ((k < kSmallPrefix ? k : kSmallPrefix) & 1));
+    const size_t merge_region = (size_t)G * 12 + 128 + (size_t)G * kp * 8 + (size_t)2 * P * 8;
     const size_t region = scan_region > merge_region ? scan_region : merge_region;
     const size_t smem = (size_t)kBins * 4 + kSmallMiscWords * 4 + small_align((size_t)M * 16, 16) +
                         (size_t)((nch + 2) / 2 * 2) * 8 + region;
@@ -475,7 +490,7 @@ static size_t topk_small_header_bytes(int64_t nq) {
 }
 
 int64_t topk_small_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k) {
-    const size_t qstride = ((size_t)plan.grid * k + 1) & ~(size_t)1;
+    const size_t qstride = (size_t)plan.grid * (size_t)(k + (k & 1));
     return (int64_t)(topk_small_header_bytes(nq) + small_align((size_t)nq * plan.grid * 4, 256) +
                      (size_t)nq * qstride * 8);
 }
@@ -487,9 +502,25 @@ static int launch_small_w(const uint8_t *codes, int64_t n, int32_t M, const uint
     auto kern = topk_small_kernel<MT>;
     int rc = ensure_smem((const void *)kern, plan.smem_bytes);
     if (rc) return rc;
+    // the slot lists as a 2-D tensor {kslot, G * nq} of 64-bit keys; the
+    // merge copies the box of the first kp keys of all G lists of a query
+    auto enc = tensor_map_encoder();
+    BOLT_REQUIRE(enc, BOLT_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    const int kslot = k + (k & 1);
+    const int kp = (k < kSmallPrefix ? k : kSmallPrefix) + ((k < kSmallPrefix ? k : kSmallPrefix) & 1);
+    CUtensorMap lmap;
+    const cuuint64_t dims[2] = {(cuuint64_t)kslot, (cuuint64_t)plan.grid * (cuuint64_t)nq};
+    const cuuint64_t strides[1] = {(cuuint64_t)kslot * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)kp, (cuuint32_t)plan.grid};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(&lmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, w.keys, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    BOLT_REQUIRE(r == CUDA_SUCCESS, BOLT_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     dim3 grid(plan.grid, (unsigned)nq);
     kern<<<grid, kSmallThreads, plan.smem_bytes, stream>>>(reinterpret_cast<const uint32_t *>(codes), n, M, luts, k,
-                                                            metric, w, plan.nbc, plan.hshift, out_sums, out_idx);
+                                                            metric, w, plan.nbc, plan.hshift, out_sums, out_idx,
+                                                            lmap);
     return check_launch("topk_small_kernel");
 }
 

@@ -21,7 +21,7 @@ from . import bolt
 
 class SearchStep:
     def __init__(self, n, J, M, nq, k, centroids, quant, metrics=(bolt.METRIC_L2, bolt.METRIC_DOT),
-                 precision=bolt.PREC_FP32, device="cuda", streams=3):
+                 precision=bolt.PREC_FP32, device="cuda", streams=8):
         self.n, self.J, self.M, self.nq, self.k = n, J, M, nq, k
         self.metrics = tuple(metrics)
         self.quant = dict(quant)  # metric -> (a, b)
