@@ -730,7 +730,7 @@ def roofline_topk(tk_ms, n, M, hbm_peak, peak_kind, kernel="topk_small_kernel"):
             # dram__bytes_read + write of one launch in an ncu --set full
             # capture of this kernel at this size (cold caches: the 8 MB of
             # codes read once; warm, as in the step, they come from L2)
-            "traffic": 8080128, "traffic_unit": "bytes per launch", "algorithmic_bytes": n * M // 2,
+            "traffic": 8082944, "traffic_unit": "bytes per launch", "algorithmic_bytes": n * M // 2,
             "peak_source": alu_peak.SOURCE,
             "one_query_per_pass_cap": round(alu_peak.lookups_per_s_one_query() / 1e12, 4),
             "hbm_equivalent_GBps": round(n * M / 2 / (tk_ms * 1e-3) / 1e9, 1), "hbm_peak_GBps": hbm_peak,
