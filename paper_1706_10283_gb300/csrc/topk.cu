@@ -16,8 +16,11 @@
 // Candidates.  Lanes append sums below the CTA's threshold to a shared
 // buffer.  When it runs full the CTA histograms the buffer by s' bin (4096
 // bins of width 2^hshift), keeps every entry up to the bin of its k-th
-// smallest and lowers its threshold: later blocks only hold larger indices,
-// so with unit bins an equal sum can no longer enter the top k.
+// smallest and lowers its threshold to just past that bin.  Warps are not in
+// lockstep, so a warp that lags can still bring a key with a lower index
+// than kept ones: thresholds stay inclusive of the k-th bin, and when the
+// CTA selects its exact k-th key instead, a tie rule rejects only keys equal
+// to it in s' with a higher index.
 //
 // Global bound.  Every CTA adds each candidate it keeps, once, to a
 // per-query global histogram of s' bins.  Those are distinct vectors, so the
@@ -300,6 +303,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     p += kBins * 4;
     uint32_t *misc = reinterpret_cast<uint32_t *>(p);
     // misc: [0] buffer count [1] insert threshold [2] failure flag [3] last CTA
+    //       [26], [27] tie rule: a key with s' == misc[26] and index > misc[27] is not inserted
     //       [4] scratch [8..26) BinSel results [32..48) keep_if counts [64..66) BlockSel
     BinSel<T> bins{hist, misc + 8, hshift};
     BlockSel<T> sel{hist, misc + 64};
@@ -315,6 +319,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         misc[2] = 0;
         misc[3] = 0;
         misc[6] = 0;  // cooperative-phase requests
+        misc[26] = 0xFFFFFFFFu;  // no tie rule
         misc[7] = 0;  // warps out of blocks
     }
     if (tid < WARPS * stages) mbar_init(&bars[tid], 1);
@@ -436,15 +441,24 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
                 kept = (int)vmisc[5];
                 for (int i = tid; i < kept; i += T) keys[i] = tmp[i];
                 __syncthreads();
-                own = hshift == 0 ? bstar : (bstar + 1u) << hshift;
+                // inclusive: a warp that lags may still bring keys equal to
+                // the bin's values with lower indices than kept ones
+                own = (bstar + 1u) << hshift;
             } else if (c_le <= gate) {
                 kept = keep_if<T>(keys, cnt, wcnt,
                                   [&](uint64_t key) { return ((uint32_t)(kv(key) >> 32) >> hshift) <= bstar; });
-                own = hshift == 0 ? bstar : (bstar + 1u) << hshift;
+                own = (bstar + 1u) << hshift;
             } else {  // one bin holds too many entries: exact k-th key
                 const uint64_t kth = sel.kth_key(keys, cnt, (uint32_t)k);
                 kept = keep_if<T>(keys, cnt, wcnt, [&](uint64_t key) { return kv(key) <= kth; });
-                own = (uint32_t)(kth >> 32);
+                // keys after the k-th key cannot enter: s' above it, or equal
+                // with a higher index (warps are not in lockstep, so a lower
+                // index can still arrive)
+                own = (uint32_t)(kth >> 32) + 1u;
+                if (tid == 0) {
+                    misc[26] = (uint32_t)(kth >> 32);
+                    misc[27] = (uint32_t)kth;
+                }
             }
             if (tid == 0) {
                 misc[0] = (uint32_t)kept;
@@ -590,6 +604,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             maybe = maybe || mh;
         }
         if (__any_sync(0xFFFFFFFFu, maybe)) {
+            uint32_t tie_v = vmisc[26], tie_i = vmisc[27];
             for (int attempt = 0;; ++attempt) {
                 // One warp prefix sum places every lane's candidates; the slots
                 // are reserved with a compare-and-swap that never passes cap.
@@ -599,7 +614,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const uint32_t sp = (pk[h][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
-                        if (valid[h] && sp < thr && (!tail[h] || v0[h] + i < (uint32_t)n)) cm |= 1u << (8 * h + i);
+                        if (valid[h] && sp < thr && (!tail[h] || v0[h] + i < (uint32_t)n) &&
+                            !(sp == tie_v && v0[h] + i > tie_i))
+                            cm |= 1u << (8 * h + i);
                     }
                 const uint32_t c = __popc(cm);
                 uint32_t incl = c;
@@ -642,6 +659,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
                 const uint32_t f = cooperative();
                 if (f & 1u) refresh_j = j + 2;
                 thr = vmisc[1];
+                tie_v = vmisc[26];
+                tie_i = vmisc[27];
             }
             if (lane == 0 && vmisc[0] > (compacted ? gate : early)) atomicOr(&misc[6], 1u);
         }

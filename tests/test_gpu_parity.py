@@ -256,6 +256,41 @@ def test_topk_sorted_input_worst_case(torch_cuda):
     check_topk(torch, codes, luts, 100, bolt.METRIC_L2)
 
 
+@pytest.mark.parametrize("pattern", ["concentrated", "sorted"])
+@pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
+def test_topk_streaming_kernel_stress(torch_cuda, pattern, metric):
+    """The streaming kernel (one query, 3,000,000 vectors) where one CTA's
+    range decides the top k: "concentrated" puts 20,000 vectors with small,
+    sparsely tied sums inside one range (its local thresholds meet the
+    global k-th sum, where warps out of lockstep matter); "sorted" makes the
+    sums decrease with the index (every block improves the threshold).
+    Twelve repeated launches must all equal the oracle."""
+    torch = torch_cuda
+    rng = np.random.default_rng(71 + metric)
+    n, M, k = 3_000_000, 16, 100
+    luts = rng.integers(0, 256, (1, M, 16)).astype(np.uint8)
+    if pattern == "concentrated":
+        codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+        # rows whose codes pick each table's 3 best entries: small sums, few ties each
+        order = np.argsort(luts[0] if metric == bolt.METRIC_L2 else -luts[0].astype(np.int32), axis=1)
+        pick = rng.integers(0, 3, (20_000, M))
+        codes[1_000_000:1_020_000] = order[np.arange(M)[None, :], pick].astype(np.uint8)
+    else:
+        luts = np.tile((np.arange(16, dtype=np.uint8) * 16)[None, None, :], (1, M, 1))
+        val = (15 - (np.arange(n) * 16 // n)).astype(np.uint8)
+        if metric == bolt.METRIC_DOT:
+            val = 15 - val
+        codes = np.repeat(val[:, None], M, axis=1)
+        codes[::7] = rng.integers(0, 16, (len(codes[::7]), M))  # break the exact ties a little
+    blocked = bolt.pack_codes(dev(torch, codes))
+    L = dev(torch, luts)
+    rs, ri = oracle.topk(oracle.scan(codes, luts), k, metric)
+    for _ in range(12):
+        s, i = bolt.topk(blocked, n, M, L, k, metric)
+        np.testing.assert_array_equal(i.cpu().numpy(), ri)
+        np.testing.assert_array_equal(s.cpu().numpy(), rs)
+
+
 def test_topk_explicit_workspace(torch_cuda):
     torch = torch_cuda
     rng = np.random.default_rng(4)
