@@ -210,15 +210,157 @@ __global__ void __launch_bounds__(kEncThreads) encode_staged_kernel(const float 
     }
 }
 
+// Two rows per lane (subspace sizes 4, 8, 16): every broadcast centroid load
+// serves both rows' packed updates, and the two rows' accumulators are
+// independent chains.  64-row tiles, 512 threads (warp w takes subspaces w,
+// w + 16, ...; lane l rows l and l + 32 of the tile).
+constexpr int kEnc2Rows = 64;
+constexpr int kEnc2Threads = 512;
+
+template <int SC>
+__device__ __forceinline__ void subspace_dists2(const float *xa, const float *xb, const float4 *cm,
+                                                uint64_t (&acc_a)[8], uint64_t (&acc_b)[8]) {
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) acc_a[k2] = acc_b[k2] = 0ull;
+#pragma unroll
+    for (int j4 = 0; j4 < SC / 4; ++j4) {
+        const float4 a4 = reinterpret_cast<const float4 *>(xa)[j4];
+        const float4 b4 = reinterpret_cast<const float4 *>(xb)[j4];
+        const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int j = 4 * j4 + jj;
+            const uint64_t xa2 = f2_pack(av[jj], av[jj]), xb2 = f2_pack(bv[jj], bv[jj]);
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+                const float4 c4 = cm[j * 4 + k4];
+                const uint64_t c01 = f2_pack(c4.x, c4.y), c23 = f2_pack(c4.z, c4.w);
+                uint64_t t = f2_sub(xa2, c01);
+                acc_a[2 * k4] = f2_fma(t, t, acc_a[2 * k4]);
+                t = f2_sub(xa2, c23);
+                acc_a[2 * k4 + 1] = f2_fma(t, t, acc_a[2 * k4 + 1]);
+                t = f2_sub(xb2, c01);
+                acc_b[2 * k4] = f2_fma(t, t, acc_b[2 * k4]);
+                t = f2_sub(xb2, c23);
+                acc_b[2 * k4 + 1] = f2_fma(t, t, acc_b[2 * k4 + 1]);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t argmin16(const uint64_t (&acc)[8]) {
+    float best = __uint_as_float((uint32_t)acc[0]);
+    uint32_t code = 0;
+#pragma unroll
+    for (int k = 1; k < kK; ++k) {
+        const float d = __uint_as_float((uint32_t)(acc[k >> 1] >> (32 * (k & 1))));
+        if (d < best) {  // strict: ties keep the lower index
+            best = d;
+            code = (uint32_t)k;
+        }
+    }
+    return code;
+}
+
+template <int SC>
+__global__ void __launch_bounds__(kEnc2Threads, 1) encode_staged2_kernel(const float *__restrict__ X, int64_t n,
+                                                                      int32_t J, int32_t M,
+                                                                      const float *__restrict__ C,
+                                                                      uint32_t *__restrict__ codes, int row_stride) {
+    extern __shared__ __align__(128) uint8_t esmem[];
+    constexpr int s = SC;
+    constexpr int W = kEnc2Threads / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *cs = reinterpret_cast<float *>(esmem);                       // [M][s][16]
+    float *xbuf = cs + (size_t)J * kK;                                   // 2 x [64][row_stride]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(xbuf + 2 * kEnc2Rows * (size_t)row_stride);
+    for (int i = tid; i < J * kK; i += kEnc2Threads) {
+        const int j = i % s, k = (i / s) % kK, m = i / (s * kK);
+        cs[((size_t)m * s + j) * kK + k] = C[i];
+    }
+    if (tid < 2) mbar_init(&bars[tid], 1);
+    fence_mbar_init();
+    __syncthreads();
+
+    const int64_t ntiles = (n + kEnc2Rows - 1) / kEnc2Rows;
+    const uint32_t row_bytes = (uint32_t)J * 4u;
+    auto issue = [&](int64_t t, int buf) {  // warp 0: one bulk copy per valid row
+        const int64_t r0 = t * kEnc2Rows;
+        const int rows = (int)min((int64_t)kEnc2Rows, n - r0);
+        if (lane == 0) mbar_arrive_expect_tx(&bars[buf], (uint32_t)rows * row_bytes);
+        __syncwarp();
+        for (int r = lane; r < rows; r += 32)
+            bulk_g2s(xbuf + ((size_t)buf * kEnc2Rows + r) * row_stride, X + (r0 + r) * J, row_bytes, &bars[buf]);
+    };
+    int64_t t = blockIdx.x;
+    if (warp == 0) {
+        if (t < ntiles) issue(t, 0);
+        if (t + gridDim.x < ntiles) issue(t + gridDim.x, 1);
+    }
+    uint32_t parbits = 0u;  // bit b: parity of buffer b's next completion
+    for (int buf = 0; t < ntiles; t += gridDim.x, buf ^= 1) {
+        const bool ok = mbar_wait_bounded(&bars[buf], (parbits >> buf) & 1u, 1000000000ull);
+        parbits ^= 1u << buf;
+        const int64_t r0 = t * kEnc2Rows;
+        const bool va = r0 + lane < n, vb = r0 + 32 + lane < n;
+        const float *xa = xbuf + ((size_t)buf * kEnc2Rows + lane) * row_stride;
+        const float *xb = xa + 32 * (size_t)row_stride;
+        for (int m = warp; m < M; m += W) {
+            uint64_t acc_a[8], acc_b[8];
+            subspace_dists2<SC>(xa + m * s, xb + m * s, reinterpret_cast<const float4 *>(cs + (size_t)m * s * kK),
+                                acc_a, acc_b);
+            uint32_t ca = (va && ok) ? argmin16(acc_a) : 0u;
+            uint32_t cb = (vb && ok) ? argmin16(acc_b) : 0u;
+            uint32_t wa = ca << (4 * (lane & 7)), wb = cb << (4 * (lane & 7));
+#pragma unroll
+            for (int off = 1; off < 8; off <<= 1) {
+                wa |= __shfl_xor_sync(0xFFFFFFFFu, wa, off);
+                wb |= __shfl_xor_sync(0xFFFFFFFFu, wb, off);
+            }
+            if ((lane & 7) == 0) {
+                const int64_t v = r0 + lane;  // r0 is a multiple of 64: 8-vector groups stay in one block
+                codes[((v >> 8) * M + m) * kRowWords + ((v & 255) >> 3)] = wa;
+                const int64_t v2 = v + 32;
+                codes[((v2 >> 8) * M + m) * kRowWords + ((v2 & 255) >> 3)] = wb;
+            }
+        }
+        if (t == ntiles - 1) {
+            // words of the last block past the last tile hold padding vectors: code 0
+            const int64_t v_end = r0 + kEnc2Rows;
+            const int w_end = (int)((v_end & 255) >> 3);
+            if (w_end != 0)
+                for (int m = warp; m < M; m += W)
+                    for (int w = w_end + lane; w < kRowWords; w += 32)
+                        codes[(((v_end - 1) >> 8) * M + m) * kRowWords + w] = 0u;
+        }
+        __syncthreads();  // every warp is done with this buffer
+        if (warp == 0 && t + 2 * (int64_t)gridDim.x < ntiles) issue(t + 2 * (int64_t)gridDim.x, buf);
+    }
+}
+
 int launch_encode_fp32(const float *X, int64_t n, int32_t J, int32_t M, const float *C, uint8_t *codes,
                        cudaStream_t stream) {
     if (J % 4 == 0 && aligned(X, 16)) {
         const int64_t ntiles = (n + kEncRows - 1) / kEncRows;
         if (ntiles == 0) return BOLT_OK;
         const int rs = enc_row_stride(J);
+        const int sv = J / M;
+        const size_t smem2 = (size_t)J * kK * 4 + 2 * (size_t)kEnc2Rows * rs * 4 + 2 * 8;
+        if ((sv == 4 || sv == 8 || sv == 16) && smem2 <= 220 * 1024) {
+            const int64_t nt2 = (n + kEnc2Rows - 1) / kEnc2Rows;
+            auto kern = sv == 4 ? encode_staged2_kernel<4> : sv == 8 ? encode_staged2_kernel<8> : encode_staged2_kernel<16>;
+            int rc = ensure_smem((const void *)kern, smem2);
+            if (rc) return rc;
+            int per_sm = 0;
+            BOLT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kEnc2Threads, smem2));
+            int64_t grid = nt2;
+            const int64_t cap = (int64_t)device_sm_count() * (per_sm > 0 ? per_sm : 1);
+            if (cap > 0 && grid > cap) grid = cap;
+            kern<<<(int)grid, kEnc2Threads, smem2, stream>>>(X, n, J, M, C, reinterpret_cast<uint32_t *>(codes), rs);
+            return check_launch("encode_staged2_kernel");
+        }
         const size_t smem = (size_t)J * kK * 4 + 2 * (size_t)kEncRows * rs * 4 + 2 * 8;
         if (smem <= 220 * 1024) {
-            const int sv = J / M;
             auto kern = sv == 4 ? encode_staged_kernel<4>
                         : sv == 8 ? encode_staged_kernel<8>
                         : sv == 16 ? encode_staged_kernel<16> : encode_staged_kernel<0>;
