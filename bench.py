@@ -48,7 +48,7 @@ FALLBACK_HBM = 6800.0  # GB/s, used only when MEASURED_PEAKS.json is absent
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["bolt", "reference"], default="bolt")
     ap.add_argument("--nq", type=int, default=None, help="override query count (profiling runs)")
