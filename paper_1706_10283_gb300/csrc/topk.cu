@@ -899,9 +899,14 @@ int launch_topk_stream(const uint8_t *codes, int64_t n, int32_t M, const uint8_t
     if (plan.warps == 16) {
         if (M == 8) return plan.bpi == 2 ? launch_w<16, 8, 2>(BOLT_TOPK_ARGS) : launch_w<16, 8, 1>(BOLT_TOPK_ARGS);
         if (M == 16) return plan.bpi == 2 ? launch_w<16, 16, 2>(BOLT_TOPK_ARGS) : launch_w<16, 16, 1>(BOLT_TOPK_ARGS);
+        BOLT_REQUIRE(plan.bpi == 1, BOLT_EUNSUPPORTED, "no streaming kernel for M=%d with %d blocks per unit", M,
+                     plan.bpi);
         if (M == 32) return launch_w<16, 32, 1>(BOLT_TOPK_ARGS);
         return launch_w<16, 0, 1>(BOLT_TOPK_ARGS);
     }
+    // the generic instantiations stream one block per unit
+    BOLT_REQUIRE(plan.bpi == 1, BOLT_EUNSUPPORTED, "no streaming kernel for %d warps, M=%d, %d blocks per unit",
+                 plan.warps, M, plan.bpi);
     if (plan.warps == 8) return launch_w<8, 0, 1>(BOLT_TOPK_ARGS);
     if (plan.warps == 4) return launch_w<4, 0, 1>(BOLT_TOPK_ARGS);
     return launch_w<2, 0, 1>(BOLT_TOPK_ARGS);

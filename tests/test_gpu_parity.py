@@ -413,3 +413,46 @@ def test_mixture_1m_workload_full_size(torch_cuda):
             np.testing.assert_array_equal(i.cpu().numpy(), ri)
             np.testing.assert_array_equal(s.cpu().numpy(), rs)
     del rows
+
+
+def clustered_codes(n, M, seed, clusters=256, chunk=5_000_000):
+    """Codes with the structure of an encoded mixture: each row belongs to
+    one of `clusters` groups and takes its group's code in a codebook with
+    probability 1/2, else a uniform code."""
+    rng = np.random.default_rng(seed)
+    pref = rng.integers(0, 16, (clusters, M), dtype=np.uint8)
+    out = np.empty((n, M), np.uint8)
+    for lo in range(0, n, chunk):
+        hi = min(n, lo + chunk)
+        g = rng.integers(0, clusters, hi - lo)
+        r = rng.integers(0, 32, (hi - lo, M), dtype=np.uint8)
+        out[lo:hi] = np.where(r < 16, r, pref[g])
+    return out
+
+
+def test_serve_50m_full_size_topk(torch_cuda):
+    """50,000,000 vectors, M = 16, top-100 (the serving database), launched
+    as the benchmark times it: one query per launch (fused streaming kernel)
+    and an 8-query batch (multi-query pipeline), L2 and dot tables built by
+    the oracle from mixture queries; every result against the oracle."""
+    torch = torch_cuda
+    cfg = synth.CONFIGS["serve_50m"]
+    n, J, M, k = cfg["n"], cfg["J"], cfg["M"], 100
+    codes = clustered_codes(n, M, 50)
+    blocked = bolt.pack_codes(dev(torch, codes))
+    torch.cuda.synchronize()
+    X = synth.mixture(20_000, J, 51)
+    Co = oracle.kmeans(X, M, 4, synth.kmeans_init_rows(20_000, 51))
+    Q = synth.mixture(8, J, 52)
+    for metric in (oracle.METRIC_L2, oracle.METRIC_DOT):
+        a, b, _, _ = oracle.fit_quant(oracle.lut_f32(X[:2000], Co, metric))
+        ol = oracle.quantize(oracle.lut_f32(Q, Co, metric), a, b)
+        rs, ri = oracle.topk(oracle.scan(codes, ol), k, metric)
+        L = dev(torch, ol)
+        for qi in range(2):
+            s, i = bolt.topk(blocked, n, M, L[qi:qi + 1], k, metric)
+            np.testing.assert_array_equal(i.cpu().numpy(), ri[qi:qi + 1])
+            np.testing.assert_array_equal(s.cpu().numpy(), rs[qi:qi + 1])
+        s, i = bolt.topk(blocked, n, M, L, k, metric)
+        np.testing.assert_array_equal(i.cpu().numpy(), ri)
+        np.testing.assert_array_equal(s.cpu().numpy(), rs)
