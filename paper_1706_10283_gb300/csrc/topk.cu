@@ -13,6 +13,13 @@
 // blocks through a private ring of shared-memory stages filled by 1-D TMA
 // bulk copies (non-multicast) completing on an mbarrier.
 //
+// Threshold.  Every warp counts its first unit's sums in shared two-level
+// histograms (fine bins of width 2^hshift, coarse bins of 16 fine bins);
+// after a barrier among those warps the CTA's k-th smallest first-round sum
+// gives its first threshold, and the counts up to that bin (at least k
+// distinct vectors) are added to per-query global fine and coarse
+// histograms, one add per non-empty bin.
+//
 // Candidates.  Lanes append sums below the CTA's threshold to a shared
 // buffer.  When it runs full the CTA histograms the buffer by s' bin (4096
 // bins of width 2^hshift), keeps every entry up to the bin of its k-th
@@ -22,17 +29,19 @@
 // CTA selects its exact k-th key instead, a tie rule rejects only keys equal
 // to it in s' with a higher index.
 //
-// Global bound.  Every CTA adds each candidate it keeps, once, to a
-// per-query global histogram of s' bins.  Those are distinct vectors, so the
-// bin where the histogram's running count reaches k bounds the k-th smallest
-// sum of the whole query; every CTA reads it back at compactions and every
-// 32 rounds and rejects sums in later bins.
+// Global bound.  Each vector is counted in the global histograms at most
+// once (first-round keys at seeding, later keys when a compaction or the
+// final publication adds the CTA's uncounted entries), so the bin where their
+// running count reaches k bounds the k-th smallest sum of the whole query.
+// Every 4 rounds one warp in turn reads the coarse then the fine counts and
+// lowers the CTA's threshold to that bin, without stopping the other warps.
 //
 // Merge.  Each CTA appends its candidates up to the current global bound
 // (at most 2k, else its exact top k) to a per-query list; the last CTA to
-// finish (atomic ticket) finds the final bound bin from the histogram,
-// gathers the few candidates at or below it into shared memory, selects the
-// exact k smallest keys, sorts them and writes the result.
+// finish (atomic ticket) gathers the lists into shared memory (when they
+// hold more than 1024 keys, only the keys at or below the final bound bin of
+// the global histogram), selects the exact k smallest keys, sorts them and
+// writes the result.
 #include <mutex>
 
 #include "scan_core.cuh"
@@ -49,6 +58,78 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+constexpr int kSeedBins = kBins / 16;  // coarse bins (16 fine bins each) of the two-level histograms
+
+// Barrier 1 among the first `warps` warps of the CTA (the warps that have a
+// first unit); barrier 0 is __syncthreads.
+__device__ __forceinline__ void seed_barrier(uint32_t warps) {
+    asm volatile("bar.sync 1, %0;" ::"r"(warps * 32u) : "memory");
+}
+__device__ __forceinline__ uint32_t vmisc_hist(const uint32_t *h, int i) {
+    return *reinterpret_cast<const volatile uint32_t *>(h + i);
+}
+
+// k-th bin search by one warp over a two-level histogram: coarse[256] and
+// fine[4096], fine bin f inside coarse bin f >> 4.  The coarse bin where the
+// running count reaches k, then the fine bin inside it; fbin is that fine
+// bin and in_bin the fine counts of cbin up to it.  kGlobal: counts in
+// global memory, read through L2 (they grow while being read: a fine count
+// may trail its coarse count, and without a fine hit the whole coarse bin is
+// returned).  False when the total is below k.
+template <bool kGlobal>
+__device__ __forceinline__ bool warp_kth_bin(const uint32_t *coarse, const uint32_t *fine, uint32_t k, int lane,
+                                             uint32_t &cbin, uint32_t &fbin, uint32_t &in_bin, uint32_t (&c)[8]) {
+    if (kGlobal) {
+        const uint4 *g4 = reinterpret_cast<const uint4 *>(coarse + lane * 8);
+        const uint4 a = __ldcg(g4), b = __ldcg(g4 + 1);
+        c[0] = a.x, c[1] = a.y, c[2] = a.z, c[3] = a.w, c[4] = b.x, c[5] = b.y, c[6] = b.z, c[7] = b.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) c[i] = reinterpret_cast<const volatile uint32_t *>(coarse)[lane * 8 + i];
+    }
+    uint32_t tot = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) tot += c[i];
+    uint32_t incl = tot;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += t;
+    }
+    const uint32_t crossing = __ballot_sync(0xFFFFFFFFu, incl >= k && incl - tot < k);
+    if (!crossing) return false;
+    const int src = __ffs(crossing) - 1;
+    uint32_t cb = 0, before = 0;
+    if (lane == src) {
+        uint32_t run = incl - tot;
+        bool hit = false;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (!hit && run + c[i] >= k) {
+                cb = (uint32_t)(lane * 8 + i);
+                before = run;
+                hit = true;
+            }
+            run += c[i];
+        }
+    }
+    cb = __shfl_sync(0xFFFFFFFFu, cb, src);
+    before = __shfl_sync(0xFFFFFFFFu, before, src);
+    uint32_t fi = 0;
+    if (lane < 16) fi = kGlobal ? __ldcg(fine + cb * 16 + lane) : reinterpret_cast<const volatile uint32_t *>(fine)[cb * 16 + lane];
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, fi, off);
+        if (lane >= off) fi += t;
+    }
+    const uint32_t hitm = __ballot_sync(0xFFFFFFFFu, lane < 16 && before + fi >= k);
+    const int fl = hitm ? __ffs(hitm) - 1 : 15;
+    cbin = cb;
+    fbin = cb * 16u + (uint32_t)fl;
+    in_bin = __shfl_sync(0xFFFFFFFFu, fi, fl);
+    return true;
 }
 
 constexpr uint64_t kFlag = 1ull << 63;  // "already counted in the global histogram"
@@ -302,6 +383,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     uint32_t *hist = reinterpret_cast<uint32_t *>(p);
     p += kBins * 4;
     uint32_t *misc = reinterpret_cast<uint32_t *>(p);
+    p += 128 * 4;
+    uint32_t *chist = reinterpret_cast<uint32_t *>(p);  // [kSeedBins] coarse counts of the first round
     // misc: [0] buffer count [1] insert threshold [2] failure flag [3] last CTA
     //       [26], [27] tie rule: a key with s' == misc[26] and index > misc[27] is not inserted
     //       [4] scratch [8..26) BinSel results [32..48) keep_if counts [64..66) BlockSel
@@ -310,6 +393,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     uint32_t *wcnt = misc + 32;
     volatile uint32_t *vmisc = misc;
     uint32_t *ghist = ws.ghist + q * kBins;
+    uint32_t *gcoarse = ws.gcoarse + q * (kBins / 16);
 
     const uint4 *lut_g = reinterpret_cast<const uint4 *>(luts + q * M * kK);
     for (int i = tid; i < M; i += T) lut[i] = lut_g[i];
@@ -322,6 +406,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         misc[26] = 0xFFFFFFFFu;  // no tie rule
         misc[7] = 0;  // warps out of blocks
     }
+    for (int i = tid; i < kBins; i += T) hist[i] = 0u;  // seeding histograms (first round)
+    for (int i = tid; i < kSeedBins; i += T) chist[i] = 0u;
     if (tid < WARPS * stages) mbar_init(&bars[tid], 1);
     fence_mbar_init();
     __syncthreads();
@@ -371,13 +457,20 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         for (int i = tid; i < cnt; i += T) {
             const uint64_t key = keys[i];
             if (!(key & kFlag)) {
-                const uint32_t bin = (uint32_t)(key >> 32) >> hshift;
-                atomicAdd(&hist[bin], 1u);
-                atomicAdd(&ghist[bin], 1u);
+                atomicAdd(&hist[(uint32_t)(key >> 32) >> hshift], 1u);
                 keys[i] = key | kFlag;
             }
         }
         __syncthreads();
+        // this CTA's new entries per bin: one global add per non-empty bin
+#pragma unroll
+        for (int i = 0; i < GPT; ++i) {
+            const uint32_t d = hist[tid + i * T] - gv[i];
+            if (d) {
+                atomicAdd(&ghist[tid + i * T], d);
+                atomicAdd(&gcoarse[(tid + i * T) >> 4], d);
+            }
+        }
         bins.find((uint32_t)k);
         const uint32_t bg = bins.res[0];
         if (tid == 0 && bg < (uint32_t)kBins) {
@@ -386,6 +479,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         }
         __syncthreads();
         return bg;
+    };
+
+    // Global bound read by one warp from the global histograms.  Counts only
+    // grow and count distinct vectors, so any snapshot gives a valid bound.
+    auto warp_refresh = [&]() {
+        uint32_t cbin, fbin, in_bin, c[8];
+        if (warp_kth_bin<true>(gcoarse, ghist, (uint32_t)k, lane, cbin, fbin, in_bin, c) && lane == 0)
+            atomicMin(&misc[1], (fbin + 1u) << hshift);
     };
 
     bool failed = false;
@@ -480,19 +581,19 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         return __shfl_sync(0xFFFFFFFFu, f, 0);
     };
 
+    // warps that have a first unit take part in seeding the threshold
+    const uint32_t seeders = u_hi > u_lo ? min((uint32_t)WARPS, u_hi - u_lo) : 0u;
     uint32_t st = 0, par = 0;  // stage and parity of this warp's current unit
     uint32_t j = 0;            // units done by this warp
-    uint32_t refresh_j = 0xFFFFFFFFu;
+
     for (uint32_t u = u_lo + warp;; u += WARPS, ++j) {
-        if (requests()) {
-            const uint32_t f = cooperative();
-            if (f & 1u) refresh_j = j + 2;  // refresh again once the other CTAs have published
-        }
+        if (requests()) cooperative();
         if (u >= u_hi || failed) break;
         if (!__all_sync(0xFFFFFFFFu, mbar_try_wait(&mybars[st], par))) {
             const bool ok = mbar_wait_bounded(&mybars[st], par, kWaitLimit);
             if (!__all_sync(0xFFFFFFFFu, ok)) {
                 failed = true;
+                if (j == 0) seed_barrier(seeders);  // the other seeders still count on this warp
                 continue;
             }
         }
@@ -562,30 +663,47 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             pk[h][3] = q4.w;
         }
         uint32_t thr = vmisc[1];
-        if (j == 0 && thr == kThrAll) {
-            // Seed the threshold from this warp's first unit: its k-th
-            // smallest s' (T) has k vectors at or below it, so no vector with
-            // s' > T can enter the top k (binary search on T, warp-wide counts).
-            auto count_le = [&](uint32_t t) -> uint32_t {
-                uint32_t c = 0;
+        if (j == 0) {
+            // Seed the threshold from the CTA's first round: every warp counts
+            // its first unit's sums in shared fine and coarse histograms;
+            // after all of them have, the k-th smallest s' of those vectors
+            // lies in fine bin b, so k vectors have s' < (b + 1) << hshift and
+            // no larger s' can enter the top k.
 #pragma unroll
-                for (int h = 0; h < BPI; ++h)
+            for (int h = 0; h < BPI; ++h)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const uint32_t sp = (pk[h][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                    if (valid[h] && (!tail[h] || v0[h] + i < (uint32_t)n)) {
+                        atomicAdd(&hist[sp >> hshift], 1u);
+                        atomicAdd(&chist[sp >> (hshift + 4)], 1u);
+                    }
+                }
+            seed_barrier(seeders);
+            uint32_t cbin, fbin, in_bin, c[8];
+            if (warp_kth_bin<false>(chist, hist, (uint32_t)k, lane, cbin, fbin, in_bin, c)) {
+                const uint32_t seed = (fbin + 1u) << hshift;
+                if (lane == 0) atomicMin(&misc[1], seed);
+                thr = min(thr, seed);
+                // Publish the first-round counts up to bin b (at least k
+                // distinct vectors, the keys inserted below) to the global
+                // histograms, one add per non-empty bin.
+                if (warp == 0) {
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const uint32_t sp = (pk[h][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
-                        c += (valid[h] && (!tail[h] || v0[h] + i < (uint32_t)n) && sp <= t) ? 1u : 0u;
+                        const uint32_t cb = (uint32_t)(lane * 8 + i);
+                        if (cb < cbin && c[i]) atomicAdd(&gcoarse[cb], c[i]);
                     }
-                return __reduce_add_sync(0xFFFFFFFFu, c);
-            };
-            if (count_le(0xFFFFu) >= (uint32_t)k) {
-                uint32_t lo = 0, hi = smax;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (count_le(mid) >= (uint32_t)k) hi = mid;
-                    else lo = mid + 1;
+                    if (lane == 0) atomicAdd(&gcoarse[cbin], in_bin);
                 }
-                if (lane == 0) atomicMin(&misc[1], lo + 1u);
-                thr = min(thr, lo + 1u);
+                for (uint32_t f0 = (uint32_t)warp * 256u; f0 <= fbin; f0 += WARPS * 256u) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const uint32_t f = f0 + (uint32_t)(lane * 8 + i);
+                        const uint32_t v = f <= fbin ? hist[f] : 0u;
+                        if (v) atomicAdd(&ghist[f], v);
+                    }
+                }
             }
         }
         bool maybe = false;
@@ -604,6 +722,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             maybe = maybe || mh;
         }
         if (__any_sync(0xFFFFFFFFu, maybe)) {
+            // first-round keys are already in the global counts (seeding)
+            const uint64_t counted = j == 0 ? kFlag : 0ull;
             uint32_t tie_v = vmisc[26], tie_i = vmisc[27];
             for (int attempt = 0;; ++attempt) {
                 // One warp prefix sum places every lane's candidates; the slots
@@ -648,7 +768,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
                         for (int i = 0; i < 8; ++i) {
                             if (cm & (1u << (8 * h + i))) {
                                 const uint32_t sp = (pk[h][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
-                                keys[pos++] = ((uint64_t)sp << 32) | (uint64_t)(v0[h] + i);
+                                keys[pos++] = ((uint64_t)sp << 32) | (uint64_t)(v0[h] + i) | counted;
                             }
                         }
                     break;
@@ -656,15 +776,16 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
                 // Buffer full: compact with the whole CTA, then retry with the
                 // tighter threshold.
                 if (lane == 0) atomicOr(&misc[6], 1u);
-                const uint32_t f = cooperative();
-                if (f & 1u) refresh_j = j + 2;
+                cooperative();
                 thr = vmisc[1];
                 tie_v = vmisc[26];
                 tie_i = vmisc[27];
             }
             if (lane == 0 && vmisc[0] > (compacted ? gate : early)) atomicOr(&misc[6], 1u);
         }
-        if (warp == 0 && lane == 0 && (j == refresh_j || (j & 31u) == 31u)) atomicOr(&misc[6], 2u);
+        // every 4 rounds one warp (in turn) lowers the threshold to the
+        // global bound
+        if ((j & 3u) == 1u && (uint32_t)warp == (j >> 2) % WARPS) warp_refresh();
     }
     // This warp is out of blocks: keep joining cooperative phases until every
     // warp is done (each of them reaches this point in bounded time).
@@ -725,11 +846,15 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     if (vmisc[3] == 0) return;
     __threadfence();
 
-    // Last CTA: final bound from the complete histogram, gather, select, sort.
+    // Last CTA: final bound from the complete histogram (unless the lists
+    // are short enough to rank whole), gather, select, sort.
     const uint32_t total = __ldcg(&ws.fill[q]);
-    bins.load_global(ghist);
-    bins.find((uint32_t)k);
-    const uint32_t bfin = bins.res[0];
+    uint32_t bfin = 0xFFFFFFFFu;
+    if (total > (uint32_t)kRankSortMax) {
+        bins.load_global(ghist);
+        bins.find((uint32_t)k);
+        bfin = bins.res[0];
+    }
     uint64_t *mk = reinterpret_cast<uint64_t *>(smem);
     if (tid == 0) misc[4] = 0;
     __syncthreads();
@@ -833,11 +958,14 @@ int plan_topk_stream(int64_t n, int32_t M, int32_t k, TopkPlan *plan) {
     plan->out_cap = (int)out_cap;
     plan->list_cap = (int)(g * out_cap);
     plan->blocks_per_cta = nu > 0 ? (nu + g - 1) / g : 0;  // units per CTA
-    plan->smem_bytes = region + align_up((size_t)M * 16, 16) + (size_t)warps * kMaxStages * 8 + kBins * 4 + 128 * 4;
+    plan->smem_bytes = region + align_up((size_t)M * 16, 16) + (size_t)warps * kMaxStages * 8 + kBins * 4 + 128 * 4 +
+                       kSeedBins * 4;
     return BOLT_OK;
 }
 
-size_t topk_header_bytes(int64_t nq) { return align_up((size_t)nq * 12, 256) + (size_t)nq * kBins * 4; }
+size_t topk_header_bytes(int64_t nq) {
+    return align_up((size_t)nq * 12, 256) + (size_t)nq * (kBins + kBins / 16) * 4;
+}
 
 int64_t topk_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k) {
     if (plan.small) return topk_small_workspace_bytes(plan, nq, k);
@@ -859,6 +987,8 @@ TopkWS carve_topk_ws(void *ws, const TopkPlan &plan, int64_t nq, int32_t k) {
     p += align_up((size_t)nq * 12, 256);
     w.ghist = reinterpret_cast<uint32_t *>(p);
     p += (size_t)nq * kBins * 4;
+    w.gcoarse = reinterpret_cast<uint32_t *>(p);
+    p += (size_t)nq * (kBins / 16) * 4;
     w.cand = reinterpret_cast<uint64_t *>(p);
     (void)plan;
     (void)k;

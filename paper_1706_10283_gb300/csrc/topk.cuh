@@ -39,6 +39,7 @@ struct TopkWS {
     uint32_t *ticket;  // [nq] CTAs finished
     uint32_t *status;  // [nq] bit 0: a bounded wait gave up
     uint32_t *ghist;   // [nq][kBins] counted candidates per sum bin
+    uint32_t *gcoarse; // [nq][kBins / 16] the same counts in bins 16 times wider
     uint64_t *cand;    // [nq][list_cap] candidate keys (sum' << 32 | index)
 };
 
