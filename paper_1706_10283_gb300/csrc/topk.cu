@@ -86,8 +86,9 @@ __device__ __forceinline__ bool warp_kth_bin(const uint32_t *coarse, const uint3
         const uint4 a = __ldcg(g4), b = __ldcg(g4 + 1);
         c[0] = a.x, c[1] = a.y, c[2] = a.z, c[3] = a.w, c[4] = b.x, c[5] = b.y, c[6] = b.z, c[7] = b.w;
     } else {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) c[i] = reinterpret_cast<const volatile uint32_t *>(coarse)[lane * 8 + i];
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(coarse + lane * 8);
+        const uint4 a = s4[0], b = s4[1];
+        c[0] = a.x, c[1] = a.y, c[2] = a.z, c[3] = a.w, c[4] = b.x, c[5] = b.y, c[6] = b.z, c[7] = b.w;
     }
     uint32_t tot = 0;
 #pragma unroll
@@ -879,12 +880,19 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     };
     const int kout = g < k ? g : k;
     if (g <= kRankSortMax) {
-        // Keys are unique: each key's rank is the number of smaller keys.
-        for (int e = tid; e < g; e += T) {
-            const uint64_t key = mk[e];
+        // Keys are unique: each key's rank is the number of smaller keys,
+        // counted by P threads (adjacent lanes) per key.
+        int P = 1;
+        while (P < 32 && g * P * 2 <= T) P <<= 1;
+        const int part = tid & (P - 1);
+        for (int base = 0; base < g; base += T / P) {
+            const int e = base + tid / P;
+            const uint64_t key = e < g ? mk[e] : ~0ull;
             int rank = 0;
-            for (int j = 0; j < g; ++j) rank += mk[j] < key ? 1 : 0;
-            if (rank < k) emit(rank, key);
+            if (e < g)
+                for (int jj = part; jj < g; jj += P) rank += mk[jj] < key ? 1 : 0;
+            for (int off = 1; off < P; off <<= 1) rank += __shfl_xor_sync(0xFFFFFFFFu, rank, off);
+            if (e < g && part == 0 && rank < k) emit(rank, key);
         }
     } else {
         const uint64_t kth = sel.kth_key(mk, g, (uint32_t)k);
