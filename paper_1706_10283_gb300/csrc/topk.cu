@@ -396,23 +396,6 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     uint32_t *ghist = ws.ghist + q * kBins;
     uint32_t *gcoarse = ws.gcoarse + q * (kBins / 16);
 
-    const uint4 *lut_g = reinterpret_cast<const uint4 *>(luts + q * M * kK);
-    for (int i = tid; i < M; i += T) lut[i] = lut_g[i];
-    if (tid == 0) {
-        misc[0] = 0;
-        misc[1] = kThrAll;
-        misc[2] = 0;
-        misc[3] = 0;
-        misc[6] = 0;  // cooperative-phase requests
-        misc[26] = 0xFFFFFFFFu;  // no tie rule
-        misc[7] = 0;  // warps out of blocks
-    }
-    for (int i = tid; i < kBins; i += T) hist[i] = 0u;  // seeding histograms (first round)
-    for (int i = tid; i < kSeedBins; i += T) chist[i] = 0u;
-    if (tid < WARPS * stages) mbar_init(&bars[tid], 1);
-    fence_mbar_init();
-    __syncthreads();
-
     // Indices fit in 32 bits (n < 2^31 vectors).  Work units are BPI
     // consecutive blocks; the CTA owns units [u_lo, u_hi).
     const uint32_t nb = (uint32_t)num_blocks(n);
@@ -430,6 +413,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     uint32_t pending = 0;  // stages with a copy in flight (lane 0)
     uint32_t phase = 0;    // parity of the next completion of each stage (lane 0)
     if (lane == 0) {
+        // each warp's ring barriers are its own: initialize them and start
+        // the first copies before the rest of the setup
+        for (int s = 0; s < stages; ++s) mbar_init(&mybars[s], 1);
+        fence_mbar_init();
         for (int s = 0; s < stages; ++s) {
             const uint32_t u = u_lo + (uint32_t)s * WARPS + warp;
             if (u < u_hi) {
@@ -440,6 +427,21 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             }
         }
     }
+
+    const uint4 *lut_g = reinterpret_cast<const uint4 *>(luts + q * M * kK);
+    for (int i = tid; i < M; i += T) lut[i] = lut_g[i];
+    if (tid == 0) {
+        misc[0] = 0;
+        misc[1] = kThrAll;
+        misc[2] = 0;
+        misc[3] = 0;
+        misc[6] = 0;  // cooperative-phase requests
+        misc[26] = 0xFFFFFFFFu;  // no tie rule
+        misc[7] = 0;  // warps out of blocks
+    }
+    for (int i = tid; i < kBins; i += T) hist[i] = 0u;  // seeding histograms (first round)
+    for (int i = tid; i < kSeedBins; i += T) chist[i] = 0u;
+    __syncthreads();
 
     // Global bound.  prefetch(): issue the loads of the global histogram into
     // registers.  finish(): hist := that snapshot plus this CTA's entries not
