@@ -854,9 +854,15 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     const uint32_t total = __ldcg(&ws.fill[q]);
     uint32_t bfin = 0xFFFFFFFFu;
     if (total > (uint32_t)kRankSortMax) {
-        bins.load_global(ghist);
-        bins.find((uint32_t)k);
-        bfin = bins.res[0];
+        // one warp reads the two-level global counts (complete: every CTA
+        // added its counts before taking its ticket)
+        if (warp == 0) {
+            uint32_t cbin, fbin, in_bin, c[8];
+            const bool ok = warp_kth_bin<true>(gcoarse, ghist, (uint32_t)k, lane, cbin, fbin, in_bin, c);
+            if (lane == 0) misc[5] = ok ? fbin : 0xFFFFFFFFu;
+        }
+        __syncthreads();
+        bfin = vmisc[5];
     }
     uint64_t *mk = reinterpret_cast<uint64_t *>(smem);
     if (tid == 0) misc[4] = 0;
