@@ -456,3 +456,46 @@ def test_serve_50m_full_size_topk(torch_cuda):
         s, i = bolt.topk(blocked, n, M, L, k, metric)
         np.testing.assert_array_equal(i.cpu().numpy(), ri)
         np.testing.assert_array_equal(s.cpu().numpy(), rs)
+
+
+def test_encode_10m_full_size(torch_cuda):
+    """10,000,000 x 256 mixture rows, M = 32, encoded in one launch by the
+    fp32 encoder and by the tensor-core encoder with fp32 re-check, as the
+    benchmark times them: the two encoders' codes equal everywhere, and the
+    codes of a seeded sample of 16,384 rows equal the oracle's."""
+    torch = torch_cuda
+    cfg = synth.CONFIGS["encode_10m"]
+    n, J, M = cfg["n"], cfg["J"], cfg["M"]
+    X = synth.mixture_torch(n, J, seed=0)
+    Co = oracle.kmeans(X[:20_000].cpu().numpy(), M, 4, synth.kmeans_init_rows(20_000, 0))
+    Cd = dev(torch, Co)
+    c32 = bolt.encode(X, Cd, bolt.PREC_FP32)
+    ctc = bolt.encode(X, Cd, bolt.PREC_BF16_RECHECK)
+    assert torch.equal(c32, ctc)
+    rows = np.sort(np.random.default_rng(12).choice(n, 16_384, replace=False))
+    Xs = X[torch.from_numpy(rows).cuda()].cpu().numpy()
+    del X
+    blocks = np.unique(rows // 256)
+    got_blocks = c32.view(-1, M * 128)[torch.from_numpy(blocks).cuda()].cpu().numpy()
+    dec = decode_blocked(got_blocks, len(blocks) * 256, M)
+    pos = np.searchsorted(blocks, rows // 256) * 256 + rows % 256
+    np.testing.assert_array_equal(dec[pos], oracle.encode(Xs, Co))
+
+
+def test_approx_matmul_full_size(torch_cuda):
+    """A (4,096 x 512) times the encoded B (100,000 x 512, M = 32), one call
+    as the benchmark and the serving mix issue it: a seeded sample of 16
+    output rows against the oracle."""
+    torch = torch_cuda
+    cfg = synth.CONFIGS["matmul_4096x512_100k"]
+    rows, n, J, M = cfg["rows"], cfg["n"], cfg["J"], cfg["M"]
+    B = synth.mixture(n, J, 31)
+    A = synth.mixture(rows, J, 32)
+    C_ = oracle.kmeans(B[:20_000], M, 4, synth.kmeans_init_rows(20_000, 31))
+    a, b, _, _ = oracle.fit_quant(oracle.lut_f32(A[:256], C_, oracle.METRIC_DOT))
+    codes = oracle.encode(B, C_)
+    blocked = bolt.pack_codes(dev(torch, codes))
+    got = bolt.approx_matmul(dev(torch, A), blocked, n, dev(torch, C_), a, b)
+    sample = np.sort(np.random.default_rng(33).choice(rows, 16, replace=False))
+    np.testing.assert_array_equal(got[torch.from_numpy(sample).cuda()].cpu().numpy(),
+                                  oracle.matmul(A[sample], codes, C_, a, b))
