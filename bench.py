@@ -684,6 +684,7 @@ def run_bolt(args, world, rank, local):
     # codes): one launch timed by itself (serial launches, graph replay)
     tk_ms = float(np.median(topk_ms))
     launch_ms = step.serial_topk_ms()
+    cold_ms = step.flushed_topk_ms()
     lookups = n * M  # one table lookup + add per (vector, codebook) for one query
     roof = roofline_topk(launch_ms, n, M, hbm_peak, peak_kind)
 
@@ -693,7 +694,11 @@ def run_bolt(args, world, rank, local):
             "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps * step.launches_per_step,
             "gpu_launches_per_step": step.launches_per_step, "roofline": roof,
             "topk_ms_per_launch": round(launch_ms, 5), "topk_ms_per_query_in_step": round(tk_ms, 5),
-            "topk_streams": len(step.side), "lookups_per_launch": lookups}
+            "topk_streams": len(step.side), "lookups_per_launch": lookups,
+            "topk_l2_flushed": {"ms_per_launch": round(cold_ms, 5),
+                                "code_GBps": round(n * M / 2 / (cold_ms * 1e-3) / 1e9, 1),
+                                "hbm_frac": round(n * M / 2 / (cold_ms * 1e-3) / 1e9 / hbm_peak, 4),
+                                "flush": "512 MB written before each launch (> 2x L2)"}}
     if rank == 0 and not args.no_aux:
         del step
         torch.cuda.empty_cache()

@@ -14,6 +14,7 @@ per-launch host overhead of the thousands of small launches is paid once.
 ``run_from_host`` adds the host->device copy of the step's inputs from pinned
 memory and the device->host copy of its results.
 """
+import numpy as np
 import torch
 
 from . import bolt
@@ -140,6 +141,25 @@ class SearchStep:
         e1.record()
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / (reps * launches)
+
+    def flushed_topk_ms(self, launches=10, flush_bytes=512 << 20, metric=bolt.METRIC_L2):
+        """Device time of one top-k launch with cold caches: before each
+        launch a buffer of flush_bytes (several times the L2) is written, and
+        only the launch (header memset + kernel) lies between the events."""
+        buf = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda")
+        pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(launches)]
+        for q, (e0, e1) in enumerate(pairs):
+            qq = q % self.nq
+            buf.zero_()
+            e0.record()
+            bolt.topk(self.codes, self.n, self.M, self.luts[metric][qq:qq + 1], self.k, metric,
+                      out_sums=self.sums[metric][qq:qq + 1], out_idx=self.idx[metric][qq:qq + 1],
+                      workspace=self.ws[0])
+            e1.record()
+        torch.cuda.synchronize()
+        del buf
+        return float(np.median([e0.elapsed_time(e1) for e0, e1 in pairs]))
 
     def topk_ms_per_launch(self):
         """Step time of the top-k segments divided by their launches (call
