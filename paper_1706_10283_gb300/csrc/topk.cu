@@ -502,82 +502,74 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     const uint32_t one = kMulOne;
     bool compacted = false;  // same value in every thread (set in cooperative())
 
-    // Cooperative phases.  Warps run independently; a warp that needs the
-    // whole CTA sets a request bit in misc[6] (1: compact the buffer, 2:
-    // refresh the global bound) and every warp joins at its next check (the
-    // request is only cleared inside the phase, between two barriers, so each
-    // warp joins each phase exactly once).
-    auto cooperative = [&]() -> uint32_t {
+    // Cooperative compaction.  Warps run independently; a warp that finds the
+    // buffer full (or above the compaction gate) sets misc[6] and every warp
+    // joins at its next check (the request is only cleared inside the phase,
+    // between two barriers, so each warp joins each phase exactly once).
+    auto cooperative = [&]() {
         __syncthreads();
-        const uint32_t f = vmisc[6];
         const int cnt = (int)vmisc[0];
-        if (f & 1u) {
-            // Keep every entry up to the bin of the k-th smallest s'.
-            prefetch();  // global histogram loads overlap the local selection
-            bins.count(keys, cnt);
-            bins.find((uint32_t)k);
-            const uint32_t bstar = bins.res[0], c_le = bins.res[1];
-            int kept;
-            uint32_t own;
-            if (cnt <= k) {
-                kept = cnt;
-                own = vmisc[1];
-            } else if (c_le <= (uint32_t)kTmpKeys) {
-                // Few survivors: append them to the (now free) histogram area,
-                // then copy them back to the front of the buffer.
-                uint64_t *tmp = reinterpret_cast<uint64_t *>(hist);
-                if (tid == 0) misc[5] = 0;
-                __syncthreads();
-                for (int i0 = 0; i0 < cnt; i0 += T) {
-                    const int i = i0 + tid;
-                    const uint64_t key = i < cnt ? keys[i] : 0ull;
-                    const bool keep = i < cnt && ((uint32_t)(kv(key) >> 32) >> hshift) <= bstar;
-                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
-                    if (bal) {
-                        const int leader = __ffs(bal) - 1;
-                        uint32_t base = 0;
-                        if (lane == leader) base = atomicAdd(&misc[5], (uint32_t)__popc(bal));
-                        base = __shfl_sync(0xFFFFFFFFu, base, leader);
-                        if (keep) tmp[base + __popc(bal & lanemask_lt())] = key;
-                    }
+        // Keep every entry up to the bin of the k-th smallest s'.
+        prefetch();  // global histogram loads overlap the local selection
+        bins.count(keys, cnt);
+        bins.find((uint32_t)k);
+        const uint32_t bstar = bins.res[0], c_le = bins.res[1];
+        int kept;
+        uint32_t own;
+        if (cnt <= k) {
+            kept = cnt;
+            own = vmisc[1];
+        } else if (c_le <= (uint32_t)kTmpKeys) {
+            // Few survivors: append them to the (now free) histogram area,
+            // then copy them back to the front of the buffer.
+            uint64_t *tmp = reinterpret_cast<uint64_t *>(hist);
+            if (tid == 0) misc[5] = 0;
+            __syncthreads();
+            for (int i0 = 0; i0 < cnt; i0 += T) {
+                const int i = i0 + tid;
+                const uint64_t key = i < cnt ? keys[i] : 0ull;
+                const bool keep = i < cnt && ((uint32_t)(kv(key) >> 32) >> hshift) <= bstar;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+                if (bal) {
+                    const int leader = __ffs(bal) - 1;
+                    uint32_t base = 0;
+                    if (lane == leader) base = atomicAdd(&misc[5], (uint32_t)__popc(bal));
+                    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+                    if (keep) tmp[base + __popc(bal & lanemask_lt())] = key;
                 }
-                __syncthreads();
-                kept = (int)vmisc[5];
-                for (int i = tid; i < kept; i += T) keys[i] = tmp[i];
-                __syncthreads();
-                // inclusive: a warp that lags may still bring keys equal to
-                // the bin's values with lower indices than kept ones
-                own = (bstar + 1u) << hshift;
-            } else if (c_le <= gate) {
-                kept = keep_if<T>(keys, cnt, wcnt,
-                                  [&](uint64_t key) { return ((uint32_t)(kv(key) >> 32) >> hshift) <= bstar; });
-                own = (bstar + 1u) << hshift;
-            } else {  // one bin holds too many entries: exact k-th key
-                const uint64_t kth = sel.kth_key(keys, cnt, (uint32_t)k);
-                kept = keep_if<T>(keys, cnt, wcnt, [&](uint64_t key) { return kv(key) <= kth; });
-                // keys after the k-th key cannot enter: s' above it, or equal
-                // with a higher index (warps are not in lockstep, so a lower
-                // index can still arrive)
-                own = (uint32_t)(kth >> 32) + 1u;
-                if (tid == 0) {
-                    misc[26] = (uint32_t)(kth >> 32);
-                    misc[27] = (uint32_t)kth;
-                }
-            }
-            if (tid == 0) {
-                misc[0] = (uint32_t)kept;
-                if (own < vmisc[1]) vmisc[1] = own;
             }
             __syncthreads();
-            finish(kept);
-            compacted = true;
-        } else {
-            prefetch();
-            finish(cnt);
+            kept = (int)vmisc[5];
+            for (int i = tid; i < kept; i += T) keys[i] = tmp[i];
+            __syncthreads();
+            // inclusive: a warp that lags may still bring keys equal to
+            // the bin's values with lower indices than kept ones
+            own = (bstar + 1u) << hshift;
+        } else if (c_le <= gate) {
+            kept = keep_if<T>(keys, cnt, wcnt,
+                              [&](uint64_t key) { return ((uint32_t)(kv(key) >> 32) >> hshift) <= bstar; });
+            own = (bstar + 1u) << hshift;
+        } else {  // one bin holds too many entries: exact k-th key
+            const uint64_t kth = sel.kth_key(keys, cnt, (uint32_t)k);
+            kept = keep_if<T>(keys, cnt, wcnt, [&](uint64_t key) { return kv(key) <= kth; });
+            // keys after the k-th key cannot enter: s' above it, or equal
+            // with a higher index (warps are not in lockstep, so a lower
+            // index can still arrive)
+            own = (uint32_t)(kth >> 32) + 1u;
+            if (tid == 0) {
+                misc[26] = (uint32_t)(kth >> 32);
+                misc[27] = (uint32_t)kth;
+            }
         }
+        if (tid == 0) {
+            misc[0] = (uint32_t)kept;
+            if (own < vmisc[1]) vmisc[1] = own;
+        }
+        __syncthreads();
+        finish(kept);
+        compacted = true;
         if (tid == 0) misc[6] = 0;
         __syncthreads();
-        return f;
     };
     auto requests = [&]() -> uint32_t {
         uint32_t f = lane == 0 ? vmisc[6] : 0u;
