@@ -40,6 +40,7 @@ def lib():
         f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
         u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
         u16p = np.ctypeslib.ndpointer(np.uint16, flags="C_CONTIGUOUS")
+        u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
         i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
         i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
         i64, i32, f32 = C.c_int64, C.c_int32, C.c_float
@@ -54,6 +55,8 @@ def lib():
             "bo_quant_params": [f32p, i64, i32, i32, C.POINTER(C.c_double), f64p],
             "bo_fit_quant": [f32p, i64, i32, C.POINTER(C.c_float), f32p, C.POINTER(C.c_int32), f64p],
             "bo_scan": [u8p, i64, i32, u8p, i64, u16p],
+            "bo_scan_u32": [u8p, i64, i32, u8p, i64, u32p],
+            "bo_dequant_u32": [u32p, i64, f32, f32, f32p],
             "bo_scan_float": [u8p, i64, i32, f32p, i64, f32p],
             "bo_topk": [u16p, i64, i64, i32, i32, u16p, i64p],
             "bo_dequant_params": [f32, f32p, i32, C.POINTER(C.c_float), C.POINTER(C.c_float)],
@@ -177,6 +180,25 @@ def scan(codes, luts):
     assert luts.shape == (nq, M, K)
     out = np.empty((nq, n), np.uint16)
     _ok(lib().bo_scan(codes, n, M, luts, nq, out), "scan")
+    return out
+
+
+def scan_u32(codes, luts):
+    """Exact uint32 sums, nq x n (any M up to 4096)."""
+    codes, luts = _u8(codes), _u8(luts)
+    n, M = codes.shape
+    nq = luts.shape[0]
+    assert luts.shape == (nq, M, K)
+    out = np.empty((nq, n), np.uint32)
+    _ok(lib().bo_scan_u32(codes, n, M, luts, nq, out), "scan_u32")
+    return out
+
+
+def dequant_u32(S, a, b):
+    S = np.ascontiguousarray(S, dtype=np.uint32)
+    inv_a, bias = dequant_params(a, b)
+    out = np.empty(S.shape, np.float32)
+    _ok(lib().bo_dequant_u32(S.reshape(-1), S.size, inv_a, bias, out.reshape(-1)), "dequant_u32")
     return out
 
 

@@ -32,7 +32,8 @@
  *    the paper's grid by minimum mean squared reconstruction error, computed
  *    in fp64, ties to the smaller alpha; a and b_m are then rounded to fp32.
  *  - Scan (Sec. 3.1, approximate distance as a sum of M table entries): exact
- *    integer sum, stored as uint16 (255*M <= 65535 for M <= 256).
+ *    integer sum, stored as uint16 (255*M <= 65535 for M <= 256); for more
+ *    codebooks (up to BO_MAX_M) the same sum stored as uint32 (bo_scan_u32).
  *  - Top-k: L2 ascending sum, dot descending sum, ties to the lower index;
  *    k > N pads with index -1 and sum 0.
  *  - Dequantize (Sec. 3.2, the biases sum to one known offset): out =
@@ -57,10 +58,13 @@
  * is monotone, so nearest neighbours rank by the sum itself, ascending). */
 enum { BO_METRIC_L2 = 0, BO_METRIC_DOT = 1, BO_METRIC_L1 = 2 };
 
+/* Largest codebook count; uint16 sums (bo_scan, bo_topk) hold M <= 256. */
+#define BO_MAX_M 4096
+
 static int check_shape(int64_t n, int32_t J, int32_t M) {
     if (n < 0 || J <= 0 || M <= 0) return BO_EINVAL;
     if (J % M != 0) return BO_EUNSUPPORTED;
-    if (M > 256) return BO_EUNSUPPORTED;
+    if (M > BO_MAX_M) return BO_EUNSUPPORTED;
     return BO_OK;
 }
 
@@ -282,7 +286,7 @@ static uint8_t quantize_one(float y, float a, float b) {
 
 int bo_quantize(const float *D, int64_t nq, int32_t M, float a, const float *b,
                 uint8_t *luts) {
-    if (nq < 0 || M <= 0 || M > 256) return BO_EINVAL;
+    if (nq < 0 || M <= 0 || M > BO_MAX_M) return BO_EINVAL;
     for (int64_t q = 0; q < nq; q++)
         for (int m = 0; m < M; m++)
             for (int k = 0; k < BO_K; k++) {
@@ -340,7 +344,7 @@ static int params_for_alpha(const double *sorted, int64_t nm, int32_t M, double 
 /* fp64 parameters for grid point alpha_idx (0..7). */
 int bo_quant_params(const float *Dtrain, int64_t ntq, int32_t M, int32_t alpha_idx,
                     double *a_out, double *b_out) {
-    if (ntq <= 0 || M <= 0 || M > 256 || alpha_idx < 0 || alpha_idx > 7) return BO_EINVAL;
+    if (ntq <= 0 || M <= 0 || M > BO_MAX_M || alpha_idx < 0 || alpha_idx > 7) return BO_EINVAL;
     double *sorted = sorted_tables(Dtrain, ntq, M);
     if (!sorted) return BO_ENOMEM;
     int rc = params_for_alpha(sorted, ntq * BO_K, M, kAlphas[alpha_idx], a_out, b_out);
@@ -352,7 +356,7 @@ int bo_quant_params(const float *Dtrain, int64_t ntq, int32_t M, int32_t alpha_i
  * loss_out (nullable): the 8 losses of the grid; alpha_idx_out (nullable). */
 int bo_fit_quant(const float *Dtrain, int64_t ntq, int32_t M, float *a_out,
                  float *b_out, int32_t *alpha_idx_out, double *loss_out) {
-    if (ntq <= 0 || M <= 0 || M > 256) return BO_EINVAL;
+    if (ntq <= 0 || M <= 0 || M > BO_MAX_M) return BO_EINVAL;
     const int64_t nm = ntq * BO_K;     /* entries per table */
     const int64_t np = nm * M;         /* pooled entries */
     double *sorted = sorted_tables(Dtrain, ntq, M);
@@ -411,6 +415,24 @@ int bo_scan(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts,
                 acc += luts[(q * M + m) * BO_K + k];
             }
             sums[q * n + i] = (uint16_t)acc;
+        }
+    return BO_OK;
+}
+
+/* The same exact sum for any M up to BO_MAX_M, stored as uint32
+ * (255 * 4096 < 2^20). */
+int bo_scan_u32(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts,
+                int64_t nq, uint32_t *sums) {
+    if (n < 0 || nq < 0 || M <= 0 || M > BO_MAX_M) return BO_EINVAL;
+    for (int64_t q = 0; q < nq; q++)
+        for (int64_t i = 0; i < n; i++) {
+            uint32_t acc = 0;
+            for (int m = 0; m < M; m++) {
+                int k = codes[i * M + m];
+                if (k >= BO_K) return BO_EINVAL;
+                acc += luts[(q * M + m) * BO_K + k];
+            }
+            sums[q * n + i] = acc;
         }
     return BO_OK;
 }
@@ -479,6 +501,16 @@ int bo_dequant_params(float a, const float *b, int32_t M, float *inv_a, float *b
 }
 
 int bo_dequant(const uint16_t *S, int64_t count, float inv_a, float bias, float *out) {
+    if (count < 0) return BO_EINVAL;
+    for (int64_t i = 0; i < count; i++) {
+        float t = (float)S[i] * inv_a;
+        out[i] = t + bias;
+    }
+    return BO_OK;
+}
+
+/* uint32 sums (M > 256): the same two roundings; S < 2^24 is exact in fp32. */
+int bo_dequant_u32(const uint32_t *S, int64_t count, float inv_a, float bias, float *out) {
     if (count < 0) return BO_EINVAL;
     for (int64_t i = 0; i < count; i++) {
         float t = (float)S[i] * inv_a;

@@ -399,3 +399,75 @@ def test_lemmas_3_and_4_hold_for_reconstruction():
     assert np.all(lhs3 <= np.linalg.norm(Qd, axis=1)[:, None] * r[None, :] + 1e-9)
     lhs4 = np.abs(cdist(Qd, Xd) - cdist(Qd, xh))
     assert np.all(lhs4 <= r[None, :] + 1e-9)
+
+
+# ------------------------------------------------------------------ more than 256 codebooks (uint32 sums)
+def test_scan_u32_closed_forms_beyond_uint16():
+    """All-255 tables give 255 M exactly (past 65,535 from M = 258 on); tables
+    whose entry is the code itself give the row sum of the codes (a library
+    reduction); M = 1 picks one table entry."""
+    rng = np.random.default_rng(61)
+    for M in (257, 258, 300, 1024, 4096):
+        codes = rng.integers(0, 16, (37, M)).astype(np.uint8)
+        full = np.full((2, M, 16), 255, np.uint8)
+        np.testing.assert_array_equal(oracle.scan_u32(codes, full), np.full((2, 37), 255 * M, np.uint32))
+        ident = np.tile(np.arange(16, dtype=np.uint8), (1, M, 1))
+        np.testing.assert_array_equal(oracle.scan_u32(codes, ident)[0], codes.astype(np.int64).sum(axis=1))
+    luts = rng.integers(0, 256, (3, 1, 16)).astype(np.uint8)
+    codes = rng.integers(0, 16, (50, 1)).astype(np.uint8)
+    np.testing.assert_array_equal(oracle.scan_u32(codes, luts), luts[:, 0, codes[:, 0]])
+
+
+def test_scan_u32_splits_into_uint16_scans():
+    """The sum over M = 700 codebooks is the sum of the scans over any split
+    of the codebooks (additivity of the sum over m); for M <= 256 it equals the
+    uint16 scan."""
+    rng = np.random.default_rng(62)
+    M, n = 700, 301
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+    luts = rng.integers(0, 256, (4, M, 16)).astype(np.uint8)
+    parts = [(0, 256), (256, 512), (512, 700)]
+    want = sum(oracle.scan(codes[:, a:b], luts[:, a:b]).astype(np.int64) for a, b in parts)
+    np.testing.assert_array_equal(oracle.scan_u32(codes, luts), want)
+    np.testing.assert_array_equal(oracle.scan_u32(codes[:, :200], luts[:, :200]),
+                                  oracle.scan(codes[:, :200], luts[:, :200]))
+    # brute force on a tiny case
+    c, l = codes[:3, :300], luts[:1, :300]
+    bf = [int(sum(int(l[0, m, c[i, m]]) for m in range(300))) for i in range(3)]
+    assert oracle.scan_u32(c, l)[0].tolist() == bf
+
+
+def test_dequant_u32_matches_uint16_and_closed_form():
+    rng = np.random.default_rng(63)
+    b = rng.standard_normal(400).astype(np.float32)
+    S16 = rng.integers(0, 65536, 1000).astype(np.uint16)
+    np.testing.assert_array_equal(oracle.dequant_u32(S16.astype(np.uint32), 3.5, b), oracle.dequant(S16, 3.5, b))
+    S = np.array([0, 65536, 100_000, 255 * 4096], np.uint32)
+    zero = np.zeros(4096, np.float32)
+    np.testing.assert_array_equal(oracle.dequant_u32(S, 1.0, zero), S.astype(np.float32))
+
+
+def test_encode_and_tables_beyond_256_codebooks():
+    """M = 512, s = 2: points built from centroids encode to their indices;
+    each table entry equals the fp64 distance by a library routine (within
+    fp32 rounding) and the sum of the L2 table entries picked by a vector's
+    own codes is the squared distance to its reconstruction (Sec. 3.1
+    decomposition)."""
+    rng = np.random.default_rng(64)
+    M, s = 512, 2
+    C = rng.standard_normal((M, 16, s)).astype(np.float32)
+    want = rng.integers(0, 16, (20, M))
+    X = np.concatenate([C[m, want[:, m]] for m in range(M)], axis=1)
+    np.testing.assert_array_equal(oracle.encode(X, C), want)
+    Q = rng.standard_normal((3, M * s)).astype(np.float32)
+    D = oracle.lut_f32(Q, C, oracle.METRIC_L2)
+    ref = np.stack([cdist(Q[:, m * s:(m + 1) * s].astype(np.float64), C[m].astype(np.float64), "sqeuclidean")
+                    for m in range(M)], axis=1)
+    np.testing.assert_allclose(D, ref, rtol=1e-5, atol=1e-6)
+    picked = D[:, np.arange(M)[None, :], want[:5]].sum(axis=2)  # (3, 5)
+    dist = ((Q[:, None, :].astype(np.float64) - X[None, :5].astype(np.float64)) ** 2).sum(axis=2)
+    np.testing.assert_allclose(picked, dist, rtol=1e-5)
+    a, bq = 2.0, np.zeros(M, np.float32)
+    L = oracle.quantize(D, a, bq)
+    assert L.shape == (3, M, 16)
+    np.testing.assert_array_equal(L, np.clip(np.floor(D * np.float32(a)), 0, 255).astype(np.uint8))
