@@ -20,7 +20,10 @@
  *    the ABI.  bolt_last_error() returns this thread's last message.
  *  - Sizes: n database vectors, J dims, M codebooks (J % M == 0,
  *    1 <= M <= 256, s = J/M dims per subspace, subspace m owning dims
- *    [m*s, (m+1)*s), Sec. 3.1 "consecutive indices"), nq queries.
+ *    [m*s, (m+1)*s), Sec. 3.1 "consecutive indices"), nq queries.  The
+ *    entry points that need no uint16 sum -- layout, encode, bolt_build_luts,
+ *    bolt_scan_u32, bolt_dequantize_u32 -- accept 1 <= M <= 4096; the rest
+ *    return BOLT_EUNSUPPORTED for M > 256.
  *  - Dense float inputs are row-major fp32 (X: n x J, Q: nq x J).
  *  - centroids: fp32 [M][16][s].
  *  - Codes use the BLOCKED layout: vectors are grouped in blocks of 256; block
@@ -31,7 +34,8 @@
  *    bolt_codes_bytes(n, M) = ceil(n/256) * M * 128 bytes (16-byte aligned
  *    base required).
  *  - luts: uint8 [nq][M][16] (16 contiguous entries per query and codebook).
- *  - Scan sums are exact integers stored as uint16 (255*M <= 65280).
+ *  - Scan sums are exact integers stored as uint16 (255*M <= 65280), or
+ *    as uint32 by bolt_scan_u32 for any M up to 4096.
  *  - Top-k order: L2 ascending sum, dot descending sum, ties to the lower
  *    vector index; rows with k > n are padded with index -1 and sum 0.
  */
@@ -110,7 +114,9 @@ int bolt_encode(const float *X, int64_t n, int32_t J, int32_t M,
  * quantization beta_m.  L2: fp32 acc = fmaf(t, t, acc), t = q_j - c_j; dot:
  * acc = fmaf(q_j, c_j, acc), both in dim order from 0.  Quantization: t =
  * (y - b_m) then t * a, two fp32 roundings, floor, clamp to [0, 255], NaN to
- * 0.  a: scale (host value); b_host: M offsets in HOST memory.
+ * 0.  a: scale (host value); b_host: M offsets in HOST memory (read before
+ * the call returns; for M > 256 they are copied to a stream-ordered device
+ * buffer, so such a call cannot be captured in a CUDA graph).
  * luts: nq x M x 16 uint8.  luts_f32 (nullable): the unquantized table
  * nq x M x 16 fp32 ("Bolt No Quantize", Sec. 4.2). */
 int bolt_build_luts(const float *Q, int64_t nq, int32_t J, int32_t M,
@@ -126,6 +132,13 @@ int bolt_scan_l2(const uint8_t *codes, int64_t n, int32_t M,
                  const uint8_t *luts, int64_t nq, uint16_t *sums, void *stream);
 int bolt_scan_dot(const uint8_t *codes, int64_t n, int32_t M,
                   const uint8_t *luts, int64_t nq, uint16_t *sums, void *stream);
+
+/* The same exact sums for 1 <= M <= 4096 codebooks, as uint32 (the uint16
+ * form holds them only while 255 * M <= 65535).  The codebooks are summed in
+ * chunks of 256 in the uint16 form and the chunk sums added in 32 bits.
+ * sums: nq x n uint32, device; codes and luts 16-byte aligned. */
+int bolt_scan_u32(const uint8_t *codes, int64_t n, int32_t M,
+                  const uint8_t *luts, int64_t nq, uint32_t *sums, void *stream);
 
 /* "Bolt No Quantize" (the Sec. 4.2 ablation that skips the 8-bit tables):
  * out[q][i] = sum over m = 0..M-1 of luts_f32[q][m][code_m(x_i)], summed in
@@ -285,6 +298,10 @@ int bolt_dequant_params(float a, const float *b_host, int32_t M, float *inv_a_ho
 /* out[i] = fp32(fp32((float)S[i] * inv_a) + bias), count values. */
 int bolt_dequantize(const uint16_t *S, int64_t count, float inv_a, float bias,
                     float *out, void *stream);
+
+/* The same for uint32 sums (bolt_scan_u32; S < 2^24 converts exactly). */
+int bolt_dequantize_u32(const uint32_t *S, int64_t count, float inv_a, float bias,
+                        float *out, void *stream);
 
 /* ---------------------------------------------------------------- matmul
  * Sec. 4.4 approximate matrix product: rows of A are queries with dot

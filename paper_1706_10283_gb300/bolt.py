@@ -42,6 +42,8 @@ _SIGS = {
                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_scan_l2": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_scan_dot": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_scan_u32": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_dequantize_u32": ([C.c_void_p, C.c_int64, C.c_float, C.c_float, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_scan_float": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_topk_workspace_bytes": ([C.c_int64, C.c_int32, C.c_int64, C.c_int32], C.c_int64),
     "bolt_topk": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
@@ -213,6 +215,20 @@ def scan_dot(codes, n, M, luts, out=None, stream=None):
     return _scan(lib().bolt_scan_dot, codes, n, M, luts, out, stream)
 
 
+def scan_u32(codes, n, M, luts, out=None, stream=None):
+    """Exact sums for any M up to 4096: (nq, n) int32 tensor holding the
+    uint32 sums (all below 2^20, so the values read the same)."""
+    torch = _torch()
+    _dev(codes, torch.uint8, "codes")
+    _dev(luts, torch.uint8, "luts")
+    nq = luts.shape[0]
+    if out is None:
+        out = torch.empty((nq, n), dtype=torch.int32, device=luts.device)
+    _dev(out, torch.int32, "out")
+    _check(lib().bolt_scan_u32(_ptr(codes), n, M, _ptr(luts), nq, _ptr(out), _stream(stream)))
+    return out
+
+
 def scan_float(codes, n, M, luts_f32, out=None, stream=None):
     """fp32 scan over fp32 tables ("Bolt No Quantize"): (nq, n) float32."""
     torch = _torch()
@@ -308,6 +324,17 @@ def dequantize(S, a, b, out=None, stream=None):
     if out is None:
         out = torch.empty(S.shape, dtype=torch.float32, device=S.device)
     _check(lib().bolt_dequantize(_ptr(S), S.numel(), inv_a, bias, _ptr(out), _stream(stream)))
+    return out
+
+
+def dequantize_u32(S, a, b, out=None, stream=None):
+    """Dequantize uint32 sums held in an int32 tensor (scan_u32's output)."""
+    torch = _torch()
+    _dev(S, torch.int32, "S")
+    inv_a, bias = dequant_params(a, b)
+    if out is None:
+        out = torch.empty(S.shape, dtype=torch.float32, device=S.device)
+    _check(lib().bolt_dequantize_u32(_ptr(S), S.numel(), inv_a, bias, _ptr(out), _stream(stream)))
     return out
 
 

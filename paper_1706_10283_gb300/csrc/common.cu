@@ -66,6 +66,21 @@ int check_nm(int64_t n, int32_t M) {
     return BOLT_OK;
 }
 
+int check_nm_wide(int64_t n, int32_t M) {
+    BOLT_REQUIRE(n >= 0 && n < (int64_t(1) << 31), BOLT_EINVAL, "n=%lld out of range [0, 2^31)", (long long)n);
+    BOLT_REQUIRE(M >= 1, BOLT_EINVAL, "M=%d must be >= 1", M);
+    BOLT_REQUIRE(M <= kMaxWideM, BOLT_EUNSUPPORTED, "M=%d > %d is unsupported", M, kMaxWideM);
+    return BOLT_OK;
+}
+
+int check_jm_wide(int32_t J, int32_t M) {
+    BOLT_REQUIRE(J >= 1 && M >= 1, BOLT_EINVAL, "J=%d, M=%d must be >= 1", J, M);
+    BOLT_REQUIRE(M <= kMaxWideM, BOLT_EUNSUPPORTED, "M=%d > %d is unsupported", M, kMaxWideM);
+    BOLT_REQUIRE(J % M == 0, BOLT_EUNSUPPORTED, "J=%d is not a multiple of M=%d", J, M);
+    BOLT_REQUIRE(J / M <= 256, BOLT_EUNSUPPORTED, "subspace dim J/M=%d > 256 is unsupported", J / M);
+    return BOLT_OK;
+}
+
 int check_jm(int32_t J, int32_t M) {
     BOLT_REQUIRE(J >= 1 && M >= 1, BOLT_EINVAL, "J=%d, M=%d must be >= 1", J, M);
     BOLT_REQUIRE(M <= 256, BOLT_EUNSUPPORTED, "M=%d > 256 is unsupported", M);
@@ -97,14 +112,14 @@ const char *bolt_last_error(void) { return bolt::g_err; }
 const char *bolt_version(void) { return "bolt-gb300 0.1 (sm_103a)"; }
 
 int64_t bolt_codes_bytes(int64_t n, int32_t M) {
-    if (n < 0 || M < 1 || M > 256) return -1;
+    if (n < 0 || M < 1 || M > bolt::kMaxWideM) return -1;
     return bolt::num_blocks(n) * (int64_t)M * bolt::kRowBytes;
 }
 
 int bolt_dequant_params(float a, const float *b_host, int32_t M, float *inv_a_host, float *bias_host) {
     bolt::clear_error();
     BOLT_REQUIRE(b_host && inv_a_host && bias_host, BOLT_EINVAL, "null pointer");
-    BOLT_REQUIRE(M >= 1 && M <= 256, BOLT_EINVAL, "M=%d out of range", M);
+    BOLT_REQUIRE(M >= 1 && M <= bolt::kMaxWideM, BOLT_EINVAL, "M=%d out of range", M);
     BOLT_REQUIRE(a > 0.0f, BOLT_EINVAL, "scale a=%g must be > 0", (double)a);
     double tot = 0.0;
     for (int m = 0; m < M; ++m) tot += (double)b_host[m];

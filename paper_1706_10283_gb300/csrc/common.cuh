@@ -51,6 +51,11 @@ int ensure_smem(const void *func, size_t bytes);
 // Shape checks shared by the entry points.
 int check_nm(int64_t n, int32_t M);
 int check_jm(int32_t J, int32_t M);
+// Entry points without uint16 sums (layout, encode, tables, uint32 scan)
+// accept up to kMaxWideM codebooks.
+constexpr int kMaxWideM = 4096;
+int check_nm_wide(int64_t n, int32_t M);
+int check_jm_wide(int32_t J, int32_t M);
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {

@@ -396,9 +396,9 @@ int launch_encode_simple(const float *X, int64_t n, int32_t J, int32_t M, const 
 extern "C" int bolt_encode(const float *X, int64_t n, int32_t J, int32_t M, const float *centroids,
                            int32_t precision, uint8_t *codes, int64_t *n_rechecked, void *stream) {
     bolt::clear_error();
-    int rc = bolt::check_jm(J, M);
+    int rc = bolt::check_jm_wide(J, M);
     if (rc) return rc;
-    rc = bolt::check_nm(n, M);
+    rc = bolt::check_nm_wide(n, M);
     if (rc) return rc;
     BOLT_REQUIRE(precision == BOLT_PREC_FP32 || precision == BOLT_PREC_BF16_RECHECK, BOLT_EINVAL,
                  "bad precision %d", precision);
@@ -408,7 +408,7 @@ extern "C" int bolt_encode(const float *X, int64_t n, int32_t J, int32_t M, cons
     BOLT_REQUIRE(X && centroids && codes, BOLT_EINVAL, "null pointer");
     BOLT_REQUIRE(bolt::aligned(X, 16) && bolt::aligned(codes, 16) && bolt::aligned(centroids, 16), BOLT_EINVAL,
                  "X, centroids and codes must be 16-byte aligned");
-    if (precision == BOLT_PREC_BF16_RECHECK && bolt::encode_tc_supported(J, M))
+    if (precision == BOLT_PREC_BF16_RECHECK && M <= 256 && bolt::encode_tc_supported(J, M))
         return bolt::launch_encode_tc(X, n, J, M, centroids, codes, n_rechecked, s);
     return bolt::launch_encode_fp32(X, n, J, M, centroids, codes, s);
 }

@@ -51,7 +51,7 @@ extern "C" {
 
 int bolt_pack_codes(const uint8_t *rowmajor, int64_t n, int32_t M, uint8_t *blocked, void *stream) {
     bolt::clear_error();
-    int rc = bolt::check_nm(n, M);
+    int rc = bolt::check_nm_wide(n, M);
     if (rc) return rc;
     BOLT_REQUIRE(blocked && (rowmajor || n == 0), BOLT_EINVAL, "null pointer");
     BOLT_REQUIRE(bolt::aligned(blocked, 16), BOLT_EINVAL, "blocked codes must be 16-byte aligned");
@@ -64,7 +64,7 @@ int bolt_pack_codes(const uint8_t *rowmajor, int64_t n, int32_t M, uint8_t *bloc
 
 int bolt_unpack_codes(const uint8_t *blocked, int64_t n, int32_t M, uint8_t *rowmajor, void *stream) {
     bolt::clear_error();
-    int rc = bolt::check_nm(n, M);
+    int rc = bolt::check_nm_wide(n, M);
     if (rc) return rc;
     BOLT_REQUIRE((blocked && rowmajor) || n == 0, BOLT_EINVAL, "null pointer");
     BOLT_REQUIRE(bolt::aligned(blocked, 16), BOLT_EINVAL, "blocked codes must be 16-byte aligned");

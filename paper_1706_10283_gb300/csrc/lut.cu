@@ -33,9 +33,11 @@ __device__ __forceinline__ uint8_t quantize_entry(float y, float a, float b) {
     return (uint8_t)floorf(t);
 }
 
+// b_dev (nullable): the offsets b_m in device memory, for M > 256; else qp.b.
 __global__ void build_luts_kernel(const float *__restrict__ Q, int64_t nq, int32_t J, int32_t M,
                                   const float *__restrict__ C, int32_t metric, QuantParams qp,
-                                  uint8_t *__restrict__ luts, float *__restrict__ luts_f32) {
+                                  const float *__restrict__ b_dev, uint8_t *__restrict__ luts,
+                                  float *__restrict__ luts_f32) {
     const int s = J / M;
     const int64_t total = nq * M * kK;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -45,18 +47,19 @@ __global__ void build_luts_kernel(const float *__restrict__ Q, int64_t nq, int32
         const int64_t q = t / ((int64_t)kK * M);
         const float y = lut_entry(Q + q * J + m * s, C + ((int64_t)m * kK + k) * s, s, metric);
         if (luts_f32) luts_f32[t] = y;
-        luts[t] = quantize_entry(y, qp.a, qp.b[m]);
+        luts[t] = quantize_entry(y, qp.a, b_dev ? b_dev[m] : qp.b[m]);
     }
 }
 
 int launch_build_luts(const float *Q, int64_t nq, int32_t J, int32_t M, const float *C, int32_t metric,
-                      const QuantParams &qp, uint8_t *luts, float *luts_f32, cudaStream_t stream) {
+                      const QuantParams &qp, uint8_t *luts, float *luts_f32, cudaStream_t stream,
+                      const float *b_dev) {
     const int64_t total = nq * M * kK;
     if (total == 0) return BOLT_OK;
     int64_t grid = (total + 255) / 256;
     const int64_t cap = (int64_t)device_sm_count() * 32;
     if (cap > 0 && grid > cap) grid = cap;
-    build_luts_kernel<<<(int)grid, 256, 0, stream>>>(Q, nq, J, M, C, metric, qp, luts, luts_f32);
+    build_luts_kernel<<<(int)grid, 256, 0, stream>>>(Q, nq, J, M, C, metric, qp, b_dev, luts, luts_f32);
     return check_launch("build_luts_kernel");
 }
 
@@ -74,14 +77,32 @@ extern "C" int bolt_build_luts(const float *Q, int64_t nq, int32_t J, int32_t M,
                                int32_t metric, float a, const float *b_host, uint8_t *luts, float *luts_f32,
                                void *stream) {
     bolt::clear_error();
-    int rc = bolt::check_jm(J, M);
+    int rc = bolt::check_jm_wide(J, M);
     if (rc) return rc;
     BOLT_REQUIRE(nq >= 0, BOLT_EINVAL, "nq=%lld < 0", (long long)nq);
     BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT || metric == BOLT_METRIC_L1, BOLT_EINVAL,
                  "bad metric %d", metric);
     BOLT_REQUIRE(nq == 0 || (Q && centroids && luts), BOLT_EINVAL, "null pointer");
+    BOLT_REQUIRE(b_host, BOLT_EINVAL, "b_host is null");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (M <= 256) {
+        bolt::QuantParams qp;
+        rc = bolt::make_quant_params(a, b_host, M, &qp);
+        if (rc) return rc;
+        return bolt::launch_build_luts(Q, nq, J, M, centroids, metric, qp, luts, luts_f32, s);
+    }
+    // More offsets than fit in the kernel's parameters: a stream-ordered
+    // device copy, freed after the launch.
+    if (nq == 0) return BOLT_OK;
     bolt::QuantParams qp;
-    rc = bolt::make_quant_params(a, b_host, M, &qp);
-    if (rc) return rc;
-    return bolt::launch_build_luts(Q, nq, J, M, centroids, metric, qp, luts, luts_f32, (cudaStream_t)stream);
+    qp.a = a;
+    for (int m = 0; m < 256; ++m) qp.b[m] = 0.0f;
+    float *b_dev = nullptr;
+    BOLT_CUDA(cudaMallocAsync(&b_dev, (size_t)M * sizeof(float), s));
+    cudaError_t e = cudaMemcpyAsync(b_dev, b_host, (size_t)M * sizeof(float), cudaMemcpyHostToDevice, s);
+    rc = e == cudaSuccess ? bolt::launch_build_luts(Q, nq, J, M, centroids, metric, qp, luts, luts_f32, s, b_dev)
+                          : BOLT_ECUDA;
+    cudaFreeAsync(b_dev, s);
+    BOLT_REQUIRE(e == cudaSuccess, BOLT_ECUDA, "bolt_build_luts: %s", cudaGetErrorString(e));
+    return rc;
 }

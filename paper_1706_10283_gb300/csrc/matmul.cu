@@ -10,10 +10,23 @@ __device__ __forceinline__ float dequant_one(uint32_t S, float inv_a, float bias
     return __fadd_rn(__fmul_rn((float)S, inv_a), bias);
 }
 
-__global__ void dequantize_kernel(const uint16_t *__restrict__ S, int64_t count, float inv_a, float bias,
+template <typename ST>
+__global__ void dequantize_kernel(const ST *__restrict__ S, int64_t count, float inv_a, float bias,
                                   float *__restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = dequant_one(S[i], inv_a, bias);
+}
+
+template <typename ST>
+static int launch_dequantize(const ST *S, int64_t count, float inv_a, float bias, float *out, cudaStream_t s) {
+    BOLT_REQUIRE(count >= 0, BOLT_EINVAL, "count < 0");
+    if (count == 0) return BOLT_OK;
+    BOLT_REQUIRE(S && out, BOLT_EINVAL, "null pointer");
+    int64_t grid = (count + 255) / 256;
+    const int64_t cap = (int64_t)device_sm_count() * 16;
+    if (cap > 0 && grid > cap) grid = cap;
+    dequantize_kernel<ST><<<(int)grid, 256, 0, s>>>(S, count, inv_a, bias, out);
+    return check_launch("dequantize_kernel");
 }
 
 // A CTA owns QB rows of A (their tables in shared memory) and strides over
@@ -73,14 +86,12 @@ extern "C" {
 
 int bolt_dequantize(const uint16_t *S, int64_t count, float inv_a, float bias, float *out, void *stream) {
     bolt::clear_error();
-    BOLT_REQUIRE(count >= 0, BOLT_EINVAL, "count < 0");
-    if (count == 0) return BOLT_OK;
-    BOLT_REQUIRE(S && out, BOLT_EINVAL, "null pointer");
-    int64_t grid = (count + 255) / 256;
-    const int64_t cap = (int64_t)bolt::device_sm_count() * 16;
-    if (cap > 0 && grid > cap) grid = cap;
-    bolt::dequantize_kernel<<<(int)grid, 256, 0, (cudaStream_t)stream>>>(S, count, inv_a, bias, out);
-    return bolt::check_launch("dequantize_kernel");
+    return bolt::launch_dequantize(S, count, inv_a, bias, out, (cudaStream_t)stream);
+}
+
+int bolt_dequantize_u32(const uint32_t *S, int64_t count, float inv_a, float bias, float *out, void *stream) {
+    bolt::clear_error();
+    return bolt::launch_dequantize(S, count, inv_a, bias, out, (cudaStream_t)stream);
 }
 
 int bolt_approx_matmul(const float *A, int64_t rows, int32_t J, const uint8_t *codesB, int64_t n, int32_t M,

@@ -52,6 +52,54 @@ static int launch_scan_sums(const uint8_t *codes, int64_t n, int32_t M, const ui
     return check_launch("scan_sums_kernel");
 }
 
+// ------------------------------------------------------------------ uint32 sums
+// Any M up to kMaxWideM: the codebooks in chunks of 256, each chunk's sums
+// exact in the uint16 form of the lookup core, added into 32-bit sums.
+__global__ void __launch_bounds__(256) scan_u32_kernel(const uint32_t *__restrict__ codes, int64_t n, int32_t M,
+                                                       const uint8_t *__restrict__ luts, int64_t nq,
+                                                       uint32_t *__restrict__ sums) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nb = num_blocks(n);
+    const int64_t items = nb * nq;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < items; item += nwarps) {
+        const int64_t q = item / nb;
+        const int64_t b = item % nb;
+        const uint4 *lut = reinterpret_cast<const uint4 *>(luts + q * M * kK);
+        const uint32_t *row = codes + b * M * kRowWords + lane;
+        uint32_t tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int m0 = 0; m0 < M; m0 += 256) {
+            const int m1 = min(M, m0 + 256);
+            Acc8 acc;
+            acc.zero();
+#pragma unroll 4
+            for (int m = m0; m < m1; ++m) {
+                const uint32_t W = __ldg(row + (int64_t)m * kRowWords);
+                acc.add(prep_word(W), __ldg(lut + m));
+            }
+            uint32_t e_lo, o_lo, e_hi, o_hi;
+            acc.finish(e_lo, o_lo, e_hi, o_hi);
+            // e = S0 | S2 << 16, o = S1 | S3 << 16 (vectors 0..3), hi: 4..7
+            tot[0] += e_lo & 0xFFFFu;
+            tot[1] += o_lo & 0xFFFFu;
+            tot[2] += e_lo >> 16;
+            tot[3] += o_lo >> 16;
+            tot[4] += e_hi & 0xFFFFu;
+            tot[5] += o_hi & 0xFFFFu;
+            tot[6] += e_hi >> 16;
+            tot[7] += o_hi >> 16;
+        }
+        const int64_t v0 = b * kBlockVecs + 8 * lane;
+        uint32_t *dst = sums + q * n + v0;
+        if (v0 + 8 <= n && aligned(dst, 16)) {
+            reinterpret_cast<uint4 *>(dst)[0] = make_uint4(tot[0], tot[1], tot[2], tot[3]);
+            reinterpret_cast<uint4 *>(dst)[1] = make_uint4(tot[4], tot[5], tot[6], tot[7]);
+        } else {
+            for (int i = 0; i < 8 && v0 + i < n; ++i) dst[i] = tot[i];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ float tables
 // "Bolt No Quantize" (Sec. 4.2 ablation): the same scan over the fp32 tables
 // D, summed in codebook order from 0 with one fp32 add per codebook.  One CTA
@@ -122,6 +170,25 @@ int bolt_scan_dot(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *lut
     int rc = bolt::check_scan_args(codes, n, M, luts, nq, sums);
     if (rc) return rc;
     return bolt::launch_scan_sums(codes, n, M, luts, nq, sums, (cudaStream_t)stream);
+}
+
+int bolt_scan_u32(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, uint32_t *sums,
+                  void *stream) {
+    bolt::clear_error();
+    int rc = bolt::check_nm_wide(n, M);
+    if (rc) return rc;
+    BOLT_REQUIRE(nq >= 0, BOLT_EINVAL, "nq=%lld < 0", (long long)nq);
+    if (n == 0 || nq == 0) return BOLT_OK;
+    BOLT_REQUIRE(codes && luts && sums, BOLT_EINVAL, "null pointer");
+    BOLT_REQUIRE(bolt::aligned(codes, 16) && bolt::aligned(luts, 16), BOLT_EINVAL,
+                 "codes and luts must be 16-byte aligned");
+    const int64_t items = bolt::num_blocks(n) * nq;
+    int64_t grid = (items + 7) / 8;
+    const int64_t cap = (int64_t)bolt::device_sm_count() * 8;
+    if (cap > 0 && grid > cap) grid = cap;
+    bolt::scan_u32_kernel<<<(int)grid, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const uint32_t *>(codes),
+                                                                         n, M, luts, nq, sums);
+    return bolt::check_launch("scan_u32_kernel");
 }
 
 int bolt_scan_float(const uint8_t *codes, int64_t n, int32_t M, const float *luts_f32, int64_t nq, float *out,

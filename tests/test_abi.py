@@ -41,12 +41,15 @@ def test_codes_bytes_layout_arithmetic():
     for M, nbytes in ((16, 8), (32, 16), (64, 32)):
         assert bolt.codes_bytes(256 * 1000, M) == 256 * 1000 * nbytes
     assert bolt.lib().bolt_codes_bytes(-1, 4) == -1
-    assert bolt.lib().bolt_codes_bytes(10, 257) == -1
+    assert bolt.lib().bolt_codes_bytes(10, 257) == 257 * 128  # up to 4096 codebooks (uint32 sums)
+    assert bolt.lib().bolt_codes_bytes(10, 4096) == 4096 * 128
+    assert bolt.lib().bolt_codes_bytes(10, 4097) == -1
+    assert bolt.lib().bolt_codes_bytes(10, 0) == -1
 
 
 def test_dequant_params_match_oracle():
     rng = np.random.default_rng(0)
-    for M in (1, 8, 32, 256):
+    for M in (1, 8, 32, 256, 1000):
         a = np.float32(rng.uniform(0.01, 10))
         b = rng.standard_normal(M).astype(np.float32) * 100
         assert bolt.dequant_params(a, b) == tuple(float(v) for v in oracle.dequant_params(a, b))

@@ -499,3 +499,59 @@ def test_approx_matmul_full_size(torch_cuda):
     sample = np.sort(np.random.default_rng(33).choice(rows, 16, replace=False))
     np.testing.assert_array_equal(got[torch.from_numpy(sample).cuda()].cpu().numpy(),
                                   oracle.matmul(A[sample], codes, C_, a, b))
+
+
+# ------------------------------------------------------------------ more than 256 codebooks
+@pytest.mark.parametrize("n,M", [(1, 1), (1000, 16), (300, 256), (5000, 257), (2049, 300), (777, 1024),
+                                 (300, 4096)])
+def test_scan_u32_bitexact(torch_cuda, n, M):
+    """uint32 sums for any M up to 4096 (chunks of 256 codebooks in the
+    uint16 form, added in 32 bits) against the oracle; for M <= 256 also the
+    uint16 scan; and the uint32 dequantization."""
+    torch = torch_cuda
+    rng = np.random.default_rng(n + M)
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+    luts = rng.integers(0, 256, (3, M, 16)).astype(np.uint8)
+    luts[1] = 255  # the largest sums: 255 M
+    blocked = bolt.pack_codes(dev(torch, codes))
+    L = dev(torch, luts)
+    got = bolt.scan_u32(blocked, n, M, L)
+    want = oracle.scan_u32(codes, luts)
+    np.testing.assert_array_equal(got.cpu().numpy().view(np.uint32), want)
+    if M <= 256:
+        np.testing.assert_array_equal(bolt.scan_l2(blocked, n, M, L).cpu().numpy(), want.astype(np.uint16))
+    b = rng.standard_normal(M).astype(np.float32)
+    np.testing.assert_array_equal(bolt.dequantize_u32(got, 0.37, b).cpu().numpy(), oracle.dequant_u32(want, 0.37, b))
+
+
+def test_more_than_256_codebooks_end_to_end(torch_cuda):
+    """M = 512 codebooks of s = 2 dims: codes (both precisions run the fp32
+    encoder), layout round trip, L2 and dot tables with the oracle's fitted
+    a and b, uint32 sums and their dequantization, all against the oracle;
+    the uint16-sum entry points refuse M > 256."""
+    torch = torch_cuda
+    n, M, s = 3000, 512, 2
+    J = M * s
+    X = synth.mixture(n, J, 71)
+    Q = synth.mixture(5, J, 72)
+    C_ = oracle.kmeans(X, M, 3, synth.kmeans_init_rows(n, 71))
+    Xd, Cd = dev(torch, X), dev(torch, C_)
+    oc = oracle.encode(X, C_)
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for prec in (bolt.PREC_FP32, bolt.PREC_BF16_RECHECK):
+        blocked = bolt.encode(Xd, Cd, prec, n_rechecked=cnt)
+        np.testing.assert_array_equal(decode_blocked(blocked.cpu().numpy(), n, M), oc)
+        assert int(cnt.item()) == 0
+    np.testing.assert_array_equal(bolt.unpack_codes(blocked, n, M).cpu().numpy(), oc)
+    for metric in (oracle.METRIC_L2, oracle.METRIC_DOT):
+        a, b, _, _ = oracle.fit_quant(oracle.lut_f32(X[:64], C_, metric))
+        luts = bolt.build_luts(dev(torch, Q), Cd, metric, a, b)
+        ol = oracle.quantize(oracle.lut_f32(Q, C_, metric), a, b)
+        np.testing.assert_array_equal(luts.cpu().numpy(), ol)
+        S = bolt.scan_u32(blocked, n, M, luts)
+        oS = oracle.scan_u32(oc, ol)
+        np.testing.assert_array_equal(S.cpu().numpy().view(np.uint32), oS)
+        np.testing.assert_array_equal(bolt.dequantize_u32(S, a, b).cpu().numpy(), oracle.dequant_u32(oS, a, b))
+        for fn in (lambda: bolt.scan_l2(blocked, n, M, luts), lambda: bolt.topk(blocked, n, M, luts, 10, metric)):
+            with pytest.raises(bolt.BoltError):
+                fn()
