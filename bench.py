@@ -722,9 +722,6 @@ def run_bolt(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-ALU_LANES_PER_SM = None  # filled from the measured integer pipe rate
-
-
 def roofline_topk(tk_ms, n, M, hbm_peak, peak_kind, kernel="topk_small_kernel"):
     """Roofline entry for the fused scan + top-k kernel (at 1M vectors the
     library runs its shared-memory size class, topk_small_kernel).  In this
