@@ -68,6 +68,11 @@ def test_invalid_arguments_are_rejected_on_host():
     # k out of range
     assert L.bolt_topk_workspace_bytes(100, 8, 1, 0) == -1
     assert L.bolt_topk_workspace_bytes(100, 8, 1, 5000) == -1
+    # top-k keeps uint16 sums: M <= 256 (the uint32 scan takes up to 4096)
+    assert L.bolt_topk_workspace_bytes(100, 257, 1, 10) == -1
+    assert L.bolt_scan_u32(nul, 10, 4097, nul, 1, nul, nul) == bolt.EUNSUPPORTED
+    assert L.bolt_scan_u32(nul, 10, 4096, nul, 1, nul, nul) == bolt.EINVAL  # passes the M check, then null
+    assert L.bolt_encode(nul, 10, 8194, 4097, nul, 0, nul, nul, nul) == bolt.EUNSUPPORTED
     # non-positive scale
     ia, bb = C.c_float(), C.c_float()
     arr = np.zeros(4, np.float32)
@@ -121,3 +126,16 @@ def test_batch_planner_rejects_bad_collections():
     # a bad record anywhere fails the whole batch
     assert _plan_bytes(_coll(100, 8, 2), _coll(100, 8, 2, qt=5)) < 0
     assert L.bolt_scan_batched(C.c_void_p(0), C.c_void_p(0)) == bolt.EINVAL
+
+
+def test_topk_workspace_query_host_only():
+    """The workspace query plans on the host: positive for every size class,
+    growing with the number of queries, -1 for invalid shapes."""
+    L = bolt.lib()
+    for n, M, k in ((1, 1, 1), (1000, 16, 10), (1_000_000, 16, 100), (50_000_000, 16, 100), (3_000_000, 32, 1000),
+                    (10, 256, 1)):
+        sizes = [L.bolt_topk_workspace_bytes(n, M, nq, k) for nq in (1, 4, 64)]
+        assert all(v > 0 for v in sizes) and sizes[0] <= sizes[1] <= sizes[2], (n, M, k, sizes)
+    assert L.bolt_topk_workspace_bytes(-1, 16, 1, 10) == -1
+    assert L.bolt_topk_workspace_bytes(100, 0, 1, 10) == -1
+    assert L.bolt_topk_workspace_bytes(100, 16, -1, 10) == -1
