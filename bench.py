@@ -397,6 +397,9 @@ def serving(codes50, C, quant, count=300, rates=(40.0, 80.0), slots=4, budget_gb
         diff = []
         for r in got:
             p = by[r.rid]
+            if r.error is not None or p.error is not None:
+                diff.append({"rid": r.rid, "failed": str(r.error or p.error)})
+                continue
             if r.kind == "matmul":
                 if not np.array_equal(r.out, p.out):
                     diff.append({"rid": r.rid, "kind": "matmul", "rows": r.nq, "batch": r.batch_id,

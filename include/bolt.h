@@ -156,7 +156,14 @@ int bolt_scan_float(const uint8_t *codes, int64_t n, int32_t M, const float *lut
  * workspace: device scratch of at least bolt_topk_workspace_bytes(n, M, nq,
  * k) bytes, 256-byte aligned, or NULL to let the library allocate and free
  * it stream-ordered (cudaMallocAsync/cudaFreeAsync) inside the call.
- * Calls sharing one workspace must not overlap on the GPU. */
+ * Calls sharing one workspace must not overlap on the GPU.
+ * Timed-out waits: every wait of the kernel on its own bulk copies is bounded
+ * (1 s).  If one gives up (only on a GPU stalled or preempted for that
+ * long), the query's row comes back with every index -2 (sums undefined).
+ * The call has already returned BOLT_OK by then, since the failure happens
+ * on the GPU after the launch: callers that read results check for index -2
+ * in column 0 and treat the row as failed (the Python binding's
+ * check_topk() and its serving loop do). */
 int64_t bolt_topk_workspace_bytes(int64_t n, int32_t M, int64_t nq, int32_t k);
 int bolt_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts,
               int64_t nq, int32_t k, int32_t metric, uint16_t *out_sums,
@@ -178,9 +185,13 @@ int bolt_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts,
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture on that device.
+ *  - The address is cached per device for the life of the process; it is
+ *    invalid after cudaDeviceReset or anything else that destroys the
+ *    device's primary context, so do not call this entry point after that.
  *  - All calls share the one array: calls that may overlap on the GPU (other
  *    streams, other host threads) race and give wrong results; serialize them
- *    (one stream, or events). */
+ *    (one stream, or events).
+ *  - A timed-out wait marks the query's row with index -2, as in bolt_topk. */
 int bolt_topk_noalloc(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts,
                       int64_t nq, int32_t k, int32_t metric, uint16_t *out_sums,
                       int64_t *out_idx, void *stream);

@@ -248,8 +248,29 @@ def topk_workspace_bytes(n, M, nq, k):
     return v
 
 
-def topk(codes, n, M, luts, k, metric, out_sums=None, out_idx=None, workspace=None, stream=None):
-    """(sums uint16 (nq, k), idx int64 (nq, k)), best first."""
+TIMED_OUT = -2  # index of every entry of a row whose bounded device wait gave up
+
+
+def check_topk(idx):
+    """Raise BoltError(ETIMEOUT) if any row of a top-k index array (torch
+    tensor or numpy array, (nq, k)) is marked as timed out (index -2 in
+    column 0: a bounded wait on the GPU gave up and the row is invalid).
+    A device tensor is read back, which waits for its stream."""
+    if idx.shape[0] == 0 or idx.shape[1] == 0:
+        return
+    col = idx[:, 0]
+    bad = col == TIMED_OUT
+    nbad = int(bad.sum())
+    if nbad:
+        raise BoltError(ETIMEOUT, "%d of %d top-k rows timed out on the GPU (a bounded wait gave up; index -2)"
+                        % (nbad, idx.shape[0]))
+
+
+def topk(codes, n, M, luts, k, metric, out_sums=None, out_idx=None, workspace=None, stream=None, check=False):
+    """(sums uint16 (nq, k), idx int64 (nq, k)), best first.  A row whose
+    bounded device wait gave up holds index -2 everywhere; check=True waits
+    for the result and raises BoltError(ETIMEOUT) for such rows (otherwise
+    call check_topk on the result before using it)."""
     torch = _torch()
     _dev(codes, torch.uint8, "codes")
     _dev(luts, torch.uint8, "luts")
@@ -262,6 +283,8 @@ def topk(codes, n, M, luts, k, metric, out_sums=None, out_idx=None, workspace=No
     wbytes = workspace.numel() if workspace is not None else 0
     _check(lib().bolt_topk(_ptr(codes), n, M, _ptr(luts), nq, k, metric, _ptr(out_sums), _ptr(out_idx),
                            _ptr(workspace), wbytes, _stream(stream)))
+    if check:
+        check_topk(out_idx)
     return out_sums, out_idx
 
 

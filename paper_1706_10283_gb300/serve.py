@@ -66,10 +66,13 @@ class Request:
     """One client request.  Q: (nq, J) float32 host array (queries, or rows
     of A for matmul).  After completion: ``idx`` (nq, k) int64 and ``dist``
     (nq, k) float32 for search, ``out`` (nq, n) float32 for matmul, and the
-    host times ``t_arrival``, ``t_dispatch``, ``t_done`` (seconds)."""
+    host times ``t_arrival``, ``t_dispatch``, ``t_done`` (seconds).
+    ``error`` is None, or the BoltError of a failed request (a search whose
+    bounded device wait gave up: its rows would hold index -2); a failed
+    request carries no results."""
 
     __slots__ = ("rid", "collection", "Q", "kind", "metric", "k", "t_arrival", "t_dispatch", "t_done", "idx",
-                 "dist", "out", "batch_id")
+                 "dist", "out", "batch_id", "error")
 
     def __init__(self, rid, collection, Q, kind=SEARCH, metric=bolt.METRIC_L2, k=10, t_arrival=0.0):
         self.rid = rid
@@ -82,6 +85,7 @@ class Request:
         self.t_dispatch = self.t_done = None
         self.idx = self.dist = self.out = None
         self.batch_id = None
+        self.error = None
 
     @property
     def nq(self):
@@ -343,8 +347,13 @@ class Server:
                     r.out = s.host_view.numpy().copy()
                 else:
                     iv, dv = s.host_view
-                    r.idx = iv[row0:row0 + r.nq, :r.k].numpy().copy()
-                    r.dist = dv[row0:row0 + r.nq, :r.k].numpy().copy()
+                    idx = iv[row0:row0 + r.nq, :r.k].numpy()
+                    try:
+                        bolt.check_topk(idx)
+                        r.idx = idx.copy()
+                        r.dist = dv[row0:row0 + r.nq, :r.k].numpy().copy()
+                    except bolt.BoltError as e:  # fail the request, never return its -2 rows
+                        r.error = e
                 r.t_done = t
                 done.append(r)
             self.budget.release(s.nbytes)
@@ -463,7 +472,11 @@ def run_plain(collections, trace, device="cuda"):
                     d = bolt.dequantize(sm, a, b, stream=s)
                     idx[i] = ix.cpu().numpy()[0]
                     dist[i] = d.cpu().numpy()[0]
-                r.idx, r.dist = idx, dist
+                try:
+                    bolt.check_topk(idx)
+                    r.idx, r.dist = idx, dist
+                except bolt.BoltError as e:
+                    r.error = e
             r.t_done = time.perf_counter()
     for r in reqs:
         r.t_arrival += base

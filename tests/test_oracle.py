@@ -302,6 +302,71 @@ def test_fit_quant_loss_matches_quantize_path():
     np.testing.assert_allclose(mse, losses[ai], rtol=2e-3)
 
 
+def _grid_losses_numpy(D):
+    """Mean squared reconstruction error (Sec. 3.2, E[(y_hat - y)^2]) for
+    every alpha of the grid, computed here in numpy from each grid point's
+    fp64 (a, b_m): beta = clamp(floor(a (y - b_m)), 0, 255), y_hat = beta / a
+    + b_m, averaged over every training entry of every table."""
+    y = D.astype(np.float64)
+    out = []
+    for i in range(8):
+        a, b = oracle.quant_params(D, i)
+        beta = np.clip(np.floor(a * (y - b[None, :, None])), 0.0, 255.0)
+        out.append(np.mean((beta / a + b[None, :, None] - y) ** 2))
+    return np.array(out)
+
+
+def _alpha_case(kind):
+    """Training tables on which the best alpha lies inside the grid.  Bulk
+    entries uniform on [0, 1) plus one entry at 2.0: with 131,072 entries
+    the outlier's clamping costs less than the coarser steps it forces at
+    alpha = 0, while large alphas clamp too much of the bulk."""
+    n = 131072
+    rng = np.random.default_rng(7)
+    if kind == "interior":
+        v = rng.uniform(0, 1, n).astype(np.float32)
+        v[0] = 2.0
+        rng.shuffle(v)
+        return v.reshape(n // 16, 1, 16)
+    if kind == "tie":
+        # 1.5% of the entries exactly 0 and 1.5% exactly 1: alpha in
+        # {.001, .002, .005, .01} picks the same quantile values (0 and 1),
+        # so those four grid points have identical parameters and losses
+        p = int(0.015 * n)
+        v = np.concatenate([np.zeros(p), np.ones(p), rng.uniform(0, 1, n - 2 * p - 1), [2.0]]).astype(np.float32)
+        rng.shuffle(v)
+        return v.reshape(n // 16, 1, 16)
+    # four tables offset by 0, 10, 20, 30 (the shared a sees y - b_m pooled)
+    v = rng.uniform(0, 1, (n // 16, 4, 16)).astype(np.float32) + np.float32([0, 10, 20, 30])[None, :, None]
+    v[5, 2, 3] = 22.0
+    return v
+
+
+@pytest.mark.parametrize("kind", ["interior", "tie", "pooled"])
+def test_fit_quant_selects_grid_argmin(kind):
+    """The fit returns the alpha with the smallest loss (Sec. 3.2: alpha is
+    chosen to minimize E[(y_hat - y)^2] over the grid), ties to the smaller
+    alpha, and the a, b of that grid point rounded to fp32.  The losses are
+    recomputed independently in numpy.  The cases put the minimum inside the
+    grid (not at its first or last point) and, for "tie", on four grid points
+    at once, so a reversed comparison, ties going to the larger alpha or
+    returning the last alpha all fail."""
+    D = _alpha_case(kind)
+    want = _grid_losses_numpy(D)
+    a, b, ai, losses = oracle.fit_quant(D)
+    np.testing.assert_allclose(losses, want, rtol=1e-9)
+    best = np.flatnonzero(want == want.min())
+    assert 0 < best[0] < 7, "case must put the minimum inside the grid"
+    if kind == "tie":
+        assert best.tolist() == [1, 2, 3, 4]
+    else:
+        # a margin far above the 1e-9 agreement, so rounding cannot move the argmin
+        assert len(best) == 1 and want.min() < (1 - 1e-6) * np.partition(want, 1)[1]
+    assert ai == best[0]
+    a64, b64 = oracle.quant_params(D, ai)
+    assert a == np.float32(a64) and np.array_equal(b, b64.astype(np.float32))
+
+
 # ------------------------------------------------------------------ scan
 def test_scan_bruteforce_exact():
     rng = np.random.default_rng(14)

@@ -1,5 +1,7 @@
-"""The usage example of README.md, at a smaller database size, with its
-top-k checked against the oracle on the same codes and tables."""
+"""The library's basic usage sequence from Python -- fit codebooks and the
+quantizer on the GPU, encode, build L2 tables, fused top-k, dequantize -- on a
+200,000-vector mixture, with the codes and the top-k checked against the
+oracle on the same codebooks and tables."""
 import numpy as np
 import pytest
 

@@ -62,3 +62,43 @@ def test_poisson_trace_is_seeded_and_in_range():
     mm = [r for r in a if r["kind"] == "matmul"]
     assert 40 <= len(mm) <= 120 and all(r["Q"].shape[1] == 8 for r in mm)
     assert all(r["Q"].shape == (r["nq"], 16) for r in a if r["kind"] == "search")
+
+
+def test_check_topk_flags_timed_out_rows():
+    from paper_1706_10283_gb300 import bolt
+
+    ok = np.array([[3, 1, 2], [0, 5, -1]], np.int64)  # -1 is padding (k > n), not a failure
+    bolt.check_topk(ok)
+    bad = ok.copy()
+    bad[1] = -2
+    with pytest.raises(bolt.BoltError) as e:
+        bolt.check_topk(bad)
+    assert e.value.code == bolt.ETIMEOUT
+
+
+def test_retire_fails_a_request_whose_rows_timed_out():
+    """A batch whose second request's rows came back as -2 (a bounded device
+    wait gave up): that request is failed with ETIMEOUT and carries no
+    results; the first request of the same batch is returned normally."""
+    from types import SimpleNamespace
+
+    import torch
+
+    from paper_1706_10283_gb300 import bolt
+    from paper_1706_10283_gb300.serve import Server
+
+    r0, r1 = req(0, 2, k=3), req(1, 1, k=3)
+    idx = torch.tensor([[4, 5, 6], [7, 8, 9], [-2, -2, -2]], dtype=torch.int64)
+    dist = torch.arange(9, dtype=torch.float32).reshape(3, 3)
+    srv = Server.__new__(Server)
+    srv.budget = Budget(100)
+    assert srv.budget.reserve(10)
+    slot = SimpleNamespace(busy=True, event=SimpleNamespace(query=lambda: True), reqs=[(r0, 0), (r1, 2)],
+                           host_view=(idx, dist), nbytes=10, keep=None)
+    srv.slots = [slot]
+    done = srv._retire()
+    assert [r.rid for r in done] == [0, 1]
+    assert r0.error is None and r0.idx.tolist() == [[4, 5, 6], [7, 8, 9]]
+    assert isinstance(r1.error, bolt.BoltError) and r1.error.code == bolt.ETIMEOUT
+    assert r1.idx is None and r1.dist is None
+    assert srv.budget.used == 0 and not slot.busy
