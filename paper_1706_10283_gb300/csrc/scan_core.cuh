@@ -23,6 +23,7 @@ namespace bolt {
 // leaving the integer ALU pipe (which runs prmt and lop3) to the lookups.
 __constant__ uint32_t kMulOne = 1u;
 __constant__ uint32_t kMulShl4 = 16u;
+__constant__ uint32_t kMulNeg256 = 0xFFFFFF00u;  // -256 mod 2^32
 
 __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
     uint32_t d;
@@ -76,8 +77,9 @@ struct Acc8 {
                                            uint32_t &o_hi) const {
         o_lo = odd_lo;
         o_hi = odd_hi;
-        e_lo = full_lo - (odd_lo << 8);
-        e_hi = full_hi - (odd_hi << 8);
+        // full - (odd << 8), as one multiply-add on the FMA pipe
+        e_lo = imad(odd_lo, kMulNeg256, full_lo);
+        e_hi = imad(odd_hi, kMulNeg256, full_hi);
     }
 };
 

@@ -500,6 +500,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     // before the first compaction: compact as soon as a few blocks are in
     const uint32_t early = min(gate, max((uint32_t)(2 * k), (uint32_t)(WARPS * BPI * kBlockVecs)));
     const uint32_t one = kMulOne;
+    const uint32_t neg1 = 0u - kMulOne;
     bool compacted = false;  // same value in every thread (set in cooperative())
 
     // Cooperative compaction.  Warps run independently; a warp that finds the
@@ -630,7 +631,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             st = 0;
             par ^= 1u;
         }
-        uint32_t pk[BPI][4], sw[BPI][4];
+        // sw[h]: the unit's 8 sums s' per lane in 16-bit lanes (s'_0 | s'_2 << 16,
+        // s'_1 | s'_3 << 16, then vectors 4..7); sum_of(h, i) is vector i's s'
+        uint32_t sw[BPI][4];
         uint32_t v0[BPI];
         bool tail[BPI], valid[BPI];
 #pragma unroll
@@ -642,21 +645,19 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             uint32_t e_lo, o_lo, e_hi, o_hi;
             acc[h].finish(e_lo, o_lo, e_hi, o_hi);
             if (metric == BOLT_METRIC_DOT) {  // s' = 255*M - S in each 16-bit lane (no borrow)
-                e_lo = smax2 - e_lo;
-                o_lo = smax2 - o_lo;
-                e_hi = smax2 - e_hi;
-                o_hi = smax2 - o_hi;
+                e_lo = imad(e_lo, neg1, smax2);
+                o_lo = imad(o_lo, neg1, smax2);
+                e_hi = imad(e_hi, neg1, smax2);
+                o_hi = imad(o_hi, neg1, smax2);
             }
             sw[h][0] = e_lo;
             sw[h][1] = o_lo;
             sw[h][2] = e_hi;
             sw[h][3] = o_hi;
-            const uint4 q4 = pack_sums(e_lo, o_lo, e_hi, o_hi);
-            pk[h][0] = q4.x;
-            pk[h][1] = q4.y;
-            pk[h][2] = q4.z;
-            pk[h][3] = q4.w;
         }
+        auto sum_of = [&](int h, int i) -> uint32_t {
+            return (sw[h][(i & 1) + 2 * (i >> 2)] >> (16 * ((i >> 1) & 1))) & 0xFFFFu;
+        };
         uint32_t thr = vmisc[1];
         if (j == 0) {
             // Seed the threshold from the CTA's first round: every warp counts
@@ -668,7 +669,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             for (int h = 0; h < BPI; ++h)
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    const uint32_t sp = (pk[h][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                    const uint32_t sp = sum_of(h, i);
                     if (valid[h] && (!tail[h] || v0[h] + i < (uint32_t)n)) {
                         atomicAdd(&hist[sp >> hshift], 1u);
                         atomicAdd(&chist[sp >> (hshift + 4)], 1u);
@@ -707,10 +708,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             bool mh = valid[h];
             if (swar && thr <= 0x7FFFu) {
                 // s' < 2^15: the top bit of (s' + 2^15 - thr) in each lane is
-                // clear exactly when s' < thr, with no borrow between lanes.
-                const uint32_t nt2 = 0u - (thr | (thr << 16));
-                const uint32_t d = imad(sw[h][0] | 0x80008000u, one, nt2) & imad(sw[h][1] | 0x80008000u, one, nt2) &
-                                   imad(sw[h][2] | 0x80008000u, one, nt2) & imad(sw[h][3] | 0x80008000u, one, nt2);
+                // clear exactly when s' < thr, with no borrow between lanes
+                // (s' | 2^15 = s' + 2^15 since bit 15 of s' is clear).
+                const uint32_t nt2 = 0x80008000u - (thr | (thr << 16));
+                const uint32_t d = imad(sw[h][0], one, nt2) & imad(sw[h][1], one, nt2) & imad(sw[h][2], one, nt2) &
+                                   imad(sw[h][3], one, nt2);
                 mh = mh && (~d & 0x80008000u) != 0u;
             }
             if (tail[h]) mh = mh && v0[h] < (uint32_t)n;
@@ -728,7 +730,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
                 for (int h = 0; h < BPI; ++h)
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const uint32_t sp = (pk[h][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                        const uint32_t sp = sum_of(h, i);
                         if (valid[h] && sp < thr && (!tail[h] || v0[h] + i < (uint32_t)n) &&
                             !(sp == tie_v && v0[h] + i > tie_i))
                             cm |= 1u << (8 * h + i);
@@ -762,7 +764,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
                             if (cm & (1u << (8 * h + i))) {
-                                const uint32_t sp = (pk[h][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                                const uint32_t sp = sum_of(h, i);
                                 keys[pos++] = ((uint64_t)sp << 32) | (uint64_t)(v0[h] + i) | counted;
                             }
                         }
