@@ -1,30 +1,39 @@
 #!/usr/bin/env python3
 """Benchmark of the Bolt hot path on GB300.
 
-Workload (default): the 1,000,000 x 128 Gaussian-mixture database with
-M = 16 codebooks (8-byte codes), 1,000 queries from the same mixture, L2 and
-dot-product top-100, one query per launch.  One step = one pass of the whole
-path: encode the database, build both query tables, scan + top-k every query
-for both metrics, dequantize the results.  The metric is encoded-vector
-distances per second: 2 metrics x 1,000 queries x 1,000,000 vectors per step.
+Workload (default, the large-N serving database): 50,000,000 x 128
+Gaussian-mixture vectors encoded with M = 16 codebooks (8-byte codes, 400 MB,
+larger than the 129 MB L2), resident on the device.  One step = one pass of
+the whole path over one batch of synthetic input:
+  1. encode a batch of 1,000,064 new database rows (an online insert into the
+     last rows of the database, Sec. 1.3; the batch holds the same vectors as
+     those rows, so the database is the same after every step),
+  2. build the uint8 query tables of 64 L2 and 64 dot-product queries,
+  3. fused scan + exact top-100 for each query, ONE QUERY PER LAUNCH (the
+     plain GPU form), the launches alternating on two CUDA streams with
+     separate workspaces, replayed from CUDA graphs,
+  4. dequantize the 128 x 100 best sums.
+The metric is encoded-vector distances per second: 128 queries x 50,000,000
+vectors per step.
 
 Also reported in the same JSON line:
-  e2e           the same step from pinned host buffers (inputs copied in,
-                results copied out inside the timed region),
-  roofline      the dominant kernel (fused scan + top-k) against its bound,
-  large_n_scan  one L2 top-100 query over a 50,000,000-vector database
-                (400 MB of codes, larger than L2) against the HBM roofline,
-  encode_10m    encode of 10,000,000 x 256 fp32 (M = 32) in input GB/s,
-  batched_collections  64 collections of uneven size scanned in one
-                persistent launch, against one launch per collection and
-                one launch per query,
-  cpu_baseline  the CPU oracle timed on a bounded sample of the same workload.
+  e2e           the same step from pinned host buffers (the insert batch and
+                the queries copied in, the results copied out) through
+                SearchStep.run_from_host,
+  roofline      the dominant kernel (topk_kernel, the streaming fused scan +
+                top-k) against the measured HBM copy bandwidth, with the
+                bare lookup core's time (bolt_probe_lookup_core) beside it,
+  cpu_baseline  the CPU oracle on this host: a seeded sample of queries over
+                the full 50M codes, one thread and all cores,
+and, as extra keys, the other configurations (1M mixture step, small i.i.d.
+workload, 64-query batch on 50M, serving trace, 10M encoder and k-means fit,
+64-collection batch, approximate matmul, accuracy).
 
 ``--impl reference`` times the CPU oracle (the only reference this method
-has) on a bounded sample per step and prints its line with "impl": "reference".
-Multi-GPU (torchrun, one process per GPU): each rank runs the same step on its
-own database shard (weak scaling, no collective on the data path); the time is
-the maximum over ranks.
+has) on a bounded sample of the same workload per step and prints its line
+with "impl": "reference".  Multi-GPU (torchrun, one process per GPU): each
+rank runs the same step on its own database (weak scaling, no collective on
+the data path); the time is the maximum over ranks.
 """
 import argparse
 import json
@@ -60,7 +69,9 @@ def parse():
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--graph-reps", type=int, default=0, help="also time graph replays of the launches")
     ap.add_argument("--collections", type=int, default=64, help="--only batch: first N collections")
-    ap.add_argument("--topk-streams", type=int, default=8, help="streams the step's one-query launches use")
+    ap.add_argument("--topk-streams", type=int, default=8, help="streams of the 1M step's one-query launches")
+    ap.add_argument("--large-streams", type=int, default=2, help="streams of the 50M step's one-query launches")
+    ap.add_argument("--large-nq", type=int, default=64, help="queries per metric in the 50M step")
     return ap.parse_args()
 
 
@@ -169,34 +180,39 @@ def workload(nq_override=None):
     return cfg
 
 
-def cpu_sample(cfg, X, Q, C, quant, rows_enc=100_000, q_sample=4):
-    """Time the CPU oracle on a bounded sample of one step and extrapolate to
-    the full step.  Returns (distances/s, seconds of CPU work, description)."""
+def oracle_step_sample(codes_host, Xins_host, Q_host, C, quant, nq_step, k, threads, q_sample=1,
+                       enc_rows=20_000):
+    """The CPU oracle on a bounded sample of one 50M step: the encode of
+    enc_rows of the insert batch, the tables of every query of the step, and
+    scan + top-k of q_sample queries per metric over all the database's
+    codes (on `threads` host threads, oracle.parallel); each part is timed
+    and scaled to the whole step.  Returns (distances/s, seconds of CPU work,
+    description)."""
     import oracle
+    from oracle import parallel
 
-    n, nq = cfg["n"], cfg["nq"]
+    n = codes_host.shape[0]
+    nx = Xins_host.shape[0]
     t0 = time.perf_counter()
-    codes = oracle.encode(X[:rows_enc], C)
+    oracle.encode(Xins_host[:enc_rows], C)
     t_enc = time.perf_counter() - t0
-    t_lut = 0.0
-    t_scan = 0.0
+    t_lut = t_scan = 0.0
     for metric in (oracle.METRIC_L2, oracle.METRIC_DOT):
         a, b = quant[metric]
         t0 = time.perf_counter()
-        luts = oracle.quantize(oracle.lut_f32(Q, C, metric), a, b)
+        luts = oracle.quantize(oracle.lut_f32(Q_host[:nq_step], C, metric), a, b)
         t_lut += time.perf_counter() - t0
-        t0 = time.perf_counter()
-        s = oracle.scan(codes, luts[:q_sample])
-        ts, ti = oracle.topk(s, cfg["k"], metric)
-        oracle.dequant(ts, a, b)
-        t_scan += time.perf_counter() - t0
-    frac = n / rows_enc
-    t_step = t_enc * frac + t_lut + t_scan * frac * (nq / q_sample)
+        for qi in range(q_sample):
+            t0 = time.perf_counter()
+            s_, _ = parallel.scan_topk(codes_host, luts[qi:qi + 1], k, metric, threads=threads)
+            oracle.dequant(s_, a, b)
+            t_scan += time.perf_counter() - t0
+    t_step = t_enc * nx / enc_rows + t_lut + t_scan * nq_step / q_sample
     work = t_enc + t_lut + t_scan
-    desc = ("oracle encode of %d of %d rows, tables for all %d queries x 2 metrics, scan + top-%d of %d queries "
-            "per metric over those %d rows; scaled to the full step" % (rows_enc, n, nq, cfg["k"], q_sample,
-                                                                      rows_enc))
-    return 2.0 * nq * n / t_step, work, desc
+    desc = ("oracle on %d host thread(s): encode of %d of the %d insert rows, tables of all %d x 2 queries, scan + "
+            "top-%d + dequantize of %d L2 and %d dot queries over all %d codes; each part scaled to the full step"
+            % (threads, enc_rows, nx, nq_step, k, q_sample, q_sample, n))
+    return 2.0 * nq_step * n / t_step, work, desc
 
 
 def prepare(cfg, data_seed, device="cuda"):
@@ -219,9 +235,12 @@ def prepare(cfg, data_seed, device="cuda"):
     return X, Q, Xd, Qd, C, quant
 
 
-def build_50m(C):
+LARGE_CHUNK = 1 << 21  # rows per generated chunk of the 50M database (a multiple of 256)
+
+
+def build_50m(C, seed_base=5000):
     """Codes of the 50,000,000 x 128 mixture database (M = 16), encoded in
-    2M-row chunks generated on the device."""
+    2M-row chunks generated on the device (chunk c from seed seed_base + c)."""
     import torch
 
     from paper_1706_10283_gb300 import bolt, synth
@@ -229,17 +248,36 @@ def build_50m(C):
     cfg = synth.CONFIGS["serve_50m"]
     n, J, M = cfg["n"], cfg["J"], cfg["M"]
     codes = torch.empty(bolt.codes_bytes(n, M), dtype=torch.uint8, device="cuda")
-    chunk = 1 << 21  # 2,097,152 rows (multiple of 256)
-    buf = torch.empty((chunk, J), dtype=torch.float32, device="cuda")
-    for lo in range(0, n, chunk):
-        hi = min(n, lo + chunk)
-        X = synth.mixture_torch(hi - lo, J, seed=5000 + lo // chunk, out=buf[:hi - lo])
+    buf = torch.empty((LARGE_CHUNK, J), dtype=torch.float32, device="cuda")
+    for lo in range(0, n, LARGE_CHUNK):
+        hi = min(n, lo + LARGE_CHUNK)
+        X = synth.mixture_torch(hi - lo, J, seed=seed_base + lo // LARGE_CHUNK, out=buf[:hi - lo])
         row0 = lo // 256 * M * 128
         bolt.encode(X, C, out=codes[row0:row0 + bolt.codes_bytes(hi - lo, M)])
     del buf
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     return codes
+
+
+INSERT_ROWS = 1_000_064  # the step's insert batch: the database's last rows
+
+
+def insert_batch(seed_base=5000):
+    """(row0, X): the vectors of rows [row0, 50M) of the database generated by
+    build_50m with the same seeds; row0 = 50M - INSERT_ROWS is a multiple of
+    256, so the batch is encoded into whole code blocks."""
+    from paper_1706_10283_gb300 import synth
+
+    cfg = synth.CONFIGS["serve_50m"]
+    n, J = cfg["n"], cfg["J"]
+    row0 = n - INSERT_ROWS
+    assert row0 % 256 == 0
+    c = row0 // LARGE_CHUNK
+    lo = c * LARGE_CHUNK
+    X = synth.mixture_torch(min(n, lo + LARGE_CHUNK) - lo, J, seed=seed_base + c)
+    assert lo + X.shape[0] == n  # the batch lies in the last chunk
+    return row0, X[row0 - lo:].contiguous()
 
 
 def accuracy_report(Xd, C, quant, nq=200, seed=21):
@@ -287,43 +325,17 @@ def accuracy_report(Xd, C, quant, nq=200, seed=21):
     return out
 
 
-def large_n_scan(codes, C, quant, hbm_peak, peak_kind):
-    """One L2 top-100 query per launch over 50,000,000 encoded vectors."""
+def batch_64_on_50m(codes, C, quant):
+    """64 L2 queries over the 50M database in one call (the multi-query
+    pipeline: every code pass shared by up to 16 queries), against the
+    one-query launches of the headline step."""
     import torch
 
     from paper_1706_10283_gb300 import bolt, synth
 
     cfg = synth.CONFIGS["serve_50m"]
     n, J, M, k = cfg["n"], cfg["J"], cfg["M"], 100
-    Q = torch.from_numpy(synth.mixture(8, J, 77)).cuda()
     a, b = quant[bolt.METRIC_L2]
-    luts = bolt.build_luts(Q, C, bolt.METRIC_L2, a, b)
-    ws = torch.empty(bolt.topk_workspace_bytes(n, M, 1, k), dtype=torch.uint8, device="cuda")
-    out_s = torch.empty((1, k), dtype=torch.uint16, device="cuda")
-    out_i = torch.empty((1, k), dtype=torch.int64, device="cuda")
-    for i in range(3):
-        bolt.topk(codes, n, M, luts[i:i + 1], k, bolt.METRIC_L2, out_s, out_i, workspace=ws)
-    torch.cuda.synchronize()
-    # device time: 8 one-query launches (each a header memset + the kernel)
-    # captured in a CUDA graph; the eager loop below is bound by host issue
-    def eight(s):
-        for i in range(8):
-            bolt.topk(codes, n, M, luts[i:i + 1], k, bolt.METRIC_L2, out_s, out_i, workspace=ws, stream=s)
-
-    ms = _graph_ms(eight, reps=3) / 8
-    reps = 24
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    ev[0].record()
-    for i in range(reps):
-        bolt.topk(codes, n, M, luts[i % 8:i % 8 + 1], k, bolt.METRIC_L2, out_s, out_i, workspace=ws)
-    ev[1].record()
-    torch.cuda.synchronize()
-    eager_ms = ev[0].elapsed_time(ev[1]) / reps
-    code_bytes = n * M / 2
-    gbs = code_bytes / (ms * 1e-3) / 1e9
-    del ws
-    # a batch of 64 queries in one call (multi-query pipeline: every code pass
-    # shared by up to 16 queries)
     Qb = torch.from_numpy(synth.mixture(64, J, 78)).cuda()
     lb = bolt.build_luts(Qb, C, bolt.METRIC_L2, a, b)
     wsb = torch.empty(bolt.topk_workspace_bytes(n, M, 64, k), dtype=torch.uint8, device="cuda")
@@ -331,18 +343,11 @@ def large_n_scan(codes, C, quant, hbm_peak, peak_kind):
     ob_i = torch.empty((64, k), dtype=torch.int64, device="cuda")
     ms_b = _graph_ms(lambda s: bolt.topk(codes, n, M, lb, k, bolt.METRIC_L2, ob_s, ob_i, workspace=wsb, stream=s),
                      reps=3)
+    bolt.check_topk(ob_i)
     del wsb
-    return {"workload": "serve_50m: 50,000,000 x 128 mixture, M=16 (400 MB codes > L2), L2 top-100, "
-                        "1 query per launch, inputs larger than L2",
-            "kernel": "topk_kernel", "ms_per_launch": round(ms, 4),
-            "timing": "CUDA graph of 8 launches, replayed 3 times between events",
-            "eager_ms_per_call": round(eager_ms, 4),
-            "distances_per_s": n / (ms * 1e-3), "code_GBps": round(gbs, 1), "hbm_peak_GBps": hbm_peak,
-            "peak": peak_kind, "frac_of_hbm": round(gbs / hbm_peak, 4),
-            "algorithmic_bytes_per_launch": code_bytes,
-            "batch_64_queries": {"ms_per_call": round(ms_b, 4), "ms_per_query": round(ms_b / 64, 4),
-                                 "distances_per_s": 64 * n / (ms_b * 1e-3),
-                                 "speedup_vs_one_query_launches": round(ms * 64 / ms_b, 2)}}
+    return {"workload": "serve_50m: 64 L2 top-100 queries in one bolt_topk call (multi-query pipeline)",
+            "ms_per_call": round(ms_b, 4), "ms_per_query": round(ms_b / 64, 4),
+            "distances_per_s": 64 * n / (ms_b * 1e-3)}
 
 
 def serving(codes50, C, quant, count=300, rates=(40.0, 80.0), slots=4, budget_gb=16.0):
@@ -427,8 +432,14 @@ def encode_10m():
     cfg = synth.CONFIGS["encode_10m"]
     n, J, M = cfg["n"], cfg["J"], cfg["M"]
     X = synth.mixture_torch(n, J, seed=0)
-    sub = X[:100_000].contiguous()
-    C = bolt.fit_codebooks(sub, M, 8, synth.kmeans_init_rows(100_000, 0))
+    # the codebooks: k-means on all 10,000,000 rows (Sec. 3.1 background,
+    # 16 Lloyd iterations from the seeded init), timed
+    iters = 16
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    C = bolt.fit_codebooks(X, M, iters, synth.kmeans_init_rows(n, 0))
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t0
     codes = torch.empty(bolt.codes_bytes(n, M), dtype=torch.uint8, device="cuda")
     out = {}
     hbm_peak, _ = peaks()
@@ -465,6 +476,9 @@ def encode_10m():
     del X, codes, codes_tc
     torch.cuda.empty_cache()
     return {"workload": "encode_10m: 10,000,000 x 256 fp32 mixture, M=32", **out,
+            "kmeans_fit": {"rows": n, "iterations": iters, "seconds": round(fit_s, 3),
+                           "ms_per_iteration": round(fit_s * 1e3 / iters, 2),
+                           "timing": "host clock around bolt_fit_codebooks (blocking), device synchronized"},
             "tensor_core_codes_equal_fp32": same,
             "sample_rows": rows, "mismatch_rate_vs_fp64": float(np.mean(c32 != c64)),
             "mse_fp32_codes": mse(c32), "mse_fp64_codes": mse(c64)}
@@ -577,71 +591,274 @@ def batched_collections():
            "roofline": {"bound": "alu", "kernel": "batch_scan_kernel",
                         "achieved": round(lookups / (batched_ms * 1e-3) / 1e12, 4),
                         "peak": round(peak / 1e12, 4), "unit": "Tlookup/s",
-                        "frac": round(lookups / (batched_ms * 1e-3) / peak, 4), "peak_source": alu_peak.SOURCE,
+                        "frac": round(lookups / (batched_ms * 1e-3) / peak, 4), "peak_source": alu_peak.source(),
                         "sums_written_GB": round(sum(c["nq"] * c["n"] * 2 for c in batch) / 1e9, 3)},
            "l2_cache": "every launch writes %.1f GB of sums (> L2)" % (sum(c["nq"] * c["n"] * 2 for c in batch) / 1e9)}
-    del plan, batch, plain
+    # the CPU oracle on a sample of the batch: one query of every collection
+    # (oracle.scan in host threads, one collection per thread), scaled to
+    # the batch's distances
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    from oracle import parallel
+
+    host = [(bolt.unpack_codes(c["codes"], c["n"], c["M"]).cpu().numpy(), c["luts"][:1].cpu().numpy())
+            for c in batch]
+    sample = sum(c["n"] for c in batch)
+    for threads in (1, parallel.host_threads()):
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda cl: oracle.scan(cl[0], cl[1]), host))
+        dt = time.perf_counter() - t0
+        res.setdefault("oracle_sample", []).append(
+            {"threads": threads, "sample": "one query per collection (%d distances)" % sample,
+             "seconds": round(dt, 3), "distances_per_s": sample / dt,
+             "batch_seconds_scaled": round(dt * dists / sample, 2)})
+    del plan, batch, plain, host
     torch.cuda.empty_cache()
     return res
 
 
 # ------------------------------------------------------------------ arms
+def clustered_codes_host(n, M, seed, clusters=256, chunk=5_000_000):
+    """Row-major codes with the structure of an encoded mixture (each row in
+    one of `clusters` groups takes its group's code in a codebook with
+    probability 1/2, else a uniform code), generated on the host: the
+    reference arm builds its database without the GPU."""
+    rng = np.random.default_rng(seed)
+    pref = rng.integers(0, 16, (clusters, M), dtype=np.uint8)
+    out = np.empty((n, M), np.uint8)
+    for lo in range(0, n, chunk):
+        hi = min(n, lo + chunk)
+        g = rng.integers(0, clusters, hi - lo)
+        r = rng.integers(0, 32, (hi - lo, M), dtype=np.uint8)
+        out[lo:hi] = np.where(r < 16, r, pref[g])
+    return out
+
+
 def run_reference(args, world, rank):
-    """CPU oracle, bounded sample per step, on this host's cores."""
+    """CPU oracle on this host's cores, on a bounded sample of the 50M step:
+    per step the encode of 2,000 insert rows, the tables of one L2 and one dot
+    query, and their scan + top-100 + dequantize over all 50M codes (all host
+    threads, oracle.parallel).  The database is built on the host (codes with
+    an encoded mixture's structure; the oracle's cost does not depend on the
+    code values)."""
     if rank != 0:
         return
     import oracle
+    from oracle import parallel
     from paper_1706_10283_gb300 import synth
 
-    cfg = workload(args.nq)
-    X = synth.mixture(cfg["n"], cfg["J"], 0)
-    Q = synth.mixture(cfg["nq"], cfg["J"], 1)
+    cfg = synth.CONFIGS["serve_50m"]
+    n, J, M, k = cfg["n"], cfg["J"], cfg["M"], 100
     fit_rows = 20_000
-    C = oracle.kmeans(X[:fit_rows], cfg["M"], 4, synth.kmeans_init_rows(fit_rows, 0))
-    Qtr = X[synth.train_query_rows(cfg["n"], 0)]
+    Xf = synth.mixture(fit_rows, J, 0)
+    C = oracle.kmeans(Xf, M, 4, synth.kmeans_init_rows(fit_rows, 0))
+    Qtr = Xf[synth.train_query_rows(fit_rows, 0)]
     quant = {}
     for m in (oracle.METRIC_L2, oracle.METRIC_DOT):
         a, b, _, _ = oracle.fit_quant(oracle.lut_f32(Qtr, C, m))
         quant[m] = (a, b)
-    vals = []
-    desc = ""
+    codes = clustered_codes_host(n, M, 50)
+    Xins = synth.mixture(2_000, J, 7)
+    Q = synth.mixture(2 * (args.warmup + args.steps), J, 1)
+    threads = parallel.host_threads()
+    times = []
     for i in range(args.warmup + args.steps):
-        v, work, desc = cpu_sample(cfg, X, Q, C, quant, rows_enc=100_000, q_sample=4)
+        t0 = time.perf_counter()
+        oracle.encode(Xins, C)
+        for j, m in enumerate((oracle.METRIC_L2, oracle.METRIC_DOT)):
+            a, b = quant[m]
+            luts = oracle.quantize(oracle.lut_f32(Q[2 * i + j:2 * i + j + 1], C, m), a, b)
+            s_, _ = parallel.scan_topk(codes, luts, k, m, threads=threads)
+            oracle.dequant(s_, a, b)
         if i >= args.warmup:
-            vals.append(v)
-    v = float(np.median(vals))
-    ms = 2.0 * cfg["nq"] * cfg["n"] / v * 1e3
+            times.append(time.perf_counter() - t0)
+    ms = float(np.mean(times)) * 1e3
+    v = 2.0 * n / (ms * 1e-3)
+    desc = ("oracle on %d host threads, per step: encode of 2,000 rows, tables and scan + top-%d + dequantize of "
+            "1 L2 and 1 dot query over all %d codes (a sample of the 50M step, which has 64 + 64 queries and a "
+            "1,000,064-row insert)" % (threads, k, n))
+    conf = config_dict(args)
+    conf["sampled"] = "per step: 2 of the 128 queries, 2,000 of the 1,000,064 insert rows"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": config_dict(cfg),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": conf,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def config_dict(cfg):
-    return {"workload": "mixture_1m", "n": cfg["n"], "dims": cfg["J"], "codebooks": cfg["M"],
-            "code_bytes_per_vector": cfg["M"] // 2, "queries": cfg["nq"], "k": cfg["k"],
-            "metrics": ["l2", "dot"], "launch": "one query per launch (CUDA graph replay; launches round-robin on several streams, "
-                      "topk_streams)",
-            "l2_cache": "inputs larger than L2: 512 MB fp32 database encoded every step"}
+def config_dict(args):
+    from paper_1706_10283_gb300 import synth
+
+    cfg = synth.CONFIGS["serve_50m"]
+    return {"workload": "serve_50m", "n": cfg["n"], "dims": cfg["J"], "codebooks": cfg["M"],
+            "code_bytes_per_vector": cfg["M"] // 2, "queries_per_step": 2 * args.large_nq, "k": 100,
+            "metrics": ["l2", "dot"], "insert_rows_per_step": INSERT_ROWS,
+            "launch": "one query per launch, alternating on %d CUDA streams (graph replay)" % args.large_streams,
+            "l2_cache": "inputs larger than L2: every pass streams the 400 MB of codes (L2 is 129 MB)"}
+
+
+def one_million_step(args, X, Q, Xd, Qd, C, quant, hbm_peak, peak_kind):
+    """The 1,000,000 x 128 mixture step (encode all rows, tables of 1,000 L2
+    and 1,000 dot queries, 2,000 one-query top-100 launches on several
+    streams, dequantize): the codes stay in L2, so its bound is the integer
+    pipe."""
+    import torch
+
+    from paper_1706_10283_gb300 import alu_peak
+    from paper_1706_10283_gb300.pipeline import SearchStep
+
+    cfg = workload(None)
+    n, J, M, nq, k = cfg["n"], cfg["J"], cfg["M"], cfg["nq"], cfg["k"]
+    step = SearchStep(n, J, M, nq, k, C, quant, streams=args.topk_streams)
+    step.set_inputs(Xd, Qd)
+    step.capture()
+    for _ in range(3):
+        step.replay()
+    torch.cuda.synchronize()
+    steps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step.replay(timed=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    per_query = step.topk_ms_per_launch()
+    launch_ms = step.serial_topk_ms()
+    cold_ms = step.flushed_topk_ms()
+    peak = alu_peak.lookups_per_s()
+    out = {"workload": "mixture_1m: 1,000,000 x 128 mixture, M=16, 1,000 queries, L2 + dot top-100, one query per "
+                       "launch on %d streams" % len(step.side),
+           "ms_per_step": round(ms, 4), "distances_per_s": 2.0 * nq * n / (ms * 1e-3),
+           "topk_ms_per_launch": round(launch_ms, 5), "topk_ms_per_query_in_step": round(per_query, 5),
+           "roofline": {"bound": "alu", "kernel": "topk_small_kernel",
+                        "achieved": round(n * M / (launch_ms * 1e-3) / 1e12, 4), "peak": round(peak / 1e12, 4),
+                        "unit": "Tlookup/s", "frac": round(n * M / (launch_ms * 1e-3) / peak, 4),
+                        "peak_source": alu_peak.source()},
+           "topk_l2_flushed": {"ms_per_launch": round(cold_ms, 5),
+                               "code_GBps": round(n * M / 2 / (cold_ms * 1e-3) / 1e9, 1),
+                               "hbm_frac": round(n * M / 2 / (cold_ms * 1e-3) / 1e9 / hbm_peak, 4),
+                               "flush": "512 MB written before each launch (> 2x L2)"}}
+    del step
+    torch.cuda.empty_cache()
+    return out
+
+
+def small_iid_step():
+    """Config 1: 10,000 x 32 i.i.d. N(0,1), M = 8, 16 queries, top-10: one
+    step (encode, L2 tables, fused top-k of the 16 queries in one call,
+    dequantize) replayed from a CUDA graph; latency-bound."""
+    import torch
+
+    from paper_1706_10283_gb300 import bolt, synth
+
+    cfg = synth.CONFIGS["small_iid_l2"]
+    n, J, M, nq, k = cfg["n"], cfg["J"], cfg["M"], cfg["nq"], cfg["k"]
+    X = torch.from_numpy(synth.iid(n, J, 0)).cuda()
+    Q = torch.from_numpy(synth.iid(nq, J, 1)).cuda()
+    C = bolt.fit_codebooks(X, M, cfg["iters"], synth.kmeans_init_rows(n, 0))
+    Qtr = X[torch.from_numpy(synth.train_query_rows(n, 0)).cuda()].contiguous()
+    a, b, _ = bolt.fit_quantizer(Qtr, C, bolt.METRIC_L2)
+    codes = torch.empty(bolt.codes_bytes(n, M), dtype=torch.uint8, device="cuda")
+    luts = torch.empty((nq, M, 16), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(bolt.topk_workspace_bytes(n, M, nq, k), dtype=torch.uint8, device="cuda")
+    os_ = torch.empty((nq, k), dtype=torch.uint16, device="cuda")
+    oi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    od = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+
+    def step(s):
+        bolt.encode(X, C, out=codes, stream=s)
+        bolt.build_luts(Q, C, bolt.METRIC_L2, a, b, out=luts, stream=s)
+        bolt.topk(codes, n, M, luts, k, bolt.METRIC_L2, os_, oi, workspace=ws, stream=s)
+        bolt.dequantize(os_, a, b, out=od, stream=s)
+
+    ms = _graph_ms(step, reps=50)
+    topk_ms = _graph_ms(lambda s: bolt.topk(codes, n, M, luts, k, bolt.METRIC_L2, os_, oi, workspace=ws, stream=s),
+                        reps=50)
+    bolt.check_topk(oi)
+    return {"workload": "small_iid_l2: 10,000 x 32 i.i.d. N(0,1), M=8, 16 queries, L2 top-10 (one top-k call)",
+            "us_per_step": round(ms * 1e3, 2), "distances_per_s": nq * n / (ms * 1e-3),
+            "topk_us_per_call": round(topk_ms * 1e3, 2), "timing": "CUDA graph replay, events around 50 replays"}
+
+
+def approx_matmul_standalone(hbm_peak):
+    """A (4096 x 512 fp32, i.i.d.) times encoded B (100,000 x 512 mixture,
+    M = 32): the full 4096 x 100,000 fp32 product (Sec. 4.4), against its
+    two bounds: integer lookups (4096 x 100,000 x 32) and the 1.64 GB
+    output write."""
+    import torch
+
+    from paper_1706_10283_gb300 import alu_peak, bolt, synth
+
+    mm = synth.CONFIGS["matmul_4096x512_100k"]
+    rows, n, J, M = mm["rows"], mm["n"], mm["J"], mm["M"]
+    B = synth.mixture_torch(n, J, seed=900)
+    CB, aB, bB = bolt.fit_codebooks(B[:50_000].contiguous(), M, 8, synth.kmeans_init_rows(50_000, 900),
+                                    Qtrain=B[torch.from_numpy(synth.train_query_rows(n, 900)).cuda()].contiguous(),
+                                    metric=bolt.METRIC_DOT)
+    codesB = bolt.encode(B, CB)
+    A = torch.from_numpy(synth.iid(rows, J, 901)).cuda()
+    out = torch.empty((rows, n), dtype=torch.float32, device="cuda")
+    ms = _graph_ms(lambda s: bolt.approx_matmul(A, codesB, n, CB, aB, bB, out=out, stream=s), reps=5)
+    lookups = rows * n * M
+    peak = alu_peak.lookups_per_s()
+    out_bytes = rows * n * 4
+    del B, out
+    torch.cuda.empty_cache()
+    return {"workload": "matmul: A 4,096 x 512 fp32 x encoded B 100,000 x 512 (M=32) -> 4,096 x 100,000 fp32",
+            "ms": round(ms, 4), "lookups": lookups,
+            "alu_bound": {"achieved_Tlookup_s": round(lookups / (ms * 1e-3) / 1e12, 4),
+                          "peak_Tlookup_s": round(peak / 1e12, 4), "frac": round(lookups / (ms * 1e-3) / peak, 4)},
+            "hbm_bound": {"output_GB": round(out_bytes / 1e9, 3),
+                          "achieved_GBps": round(out_bytes / (ms * 1e-3) / 1e9, 1), "peak_GBps": hbm_peak,
+                          "frac": round(out_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 4)}}
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one topk_kernel launch
+# (ncu, one query, 8,000,000 vectors, cold caches) scaled by 50M / 8M, or
+# None until a capture of the current kernel exists
+TOPK_TRAFFIC_50M = None
+
+
+def roofline_topk_50m(launch_ms, n, M, hbm_peak, peak_kind, core_us):
+    algo = n * M // 2  # bytes of codes one launch reads (Sec. 3.1: M/2 bytes per 4-bit code vector)
+    achieved = algo / (launch_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "topk_kernel", "achieved": round(achieved, 1), "peak": hbm_peak,
+            "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": TOPK_TRAFFIC_50M,
+            "traffic_unit": "bytes per launch", "algorithmic_bytes": algo, "peak_kind": peak_kind,
+            "launch_ms": round(launch_ms, 5),
+            "timing": "one launch by itself: 20 one-query launches on one stream in a CUDA graph, events "
+                      "around 10 replays",
+            "lookup_core_floor": {"us_per_pass": round(core_us, 2),
+                                  "frac_of_hbm": round(algo / (core_us * 1e-6) / 1e9 / hbm_peak, 4),
+                                  "launch_vs_floor": round(core_us * 1e-3 / launch_ms, 4),
+                                  "probe": "bolt_probe_lookup_core: the same blocks, tables and bulk-copy rings, "
+                                           "sums reduced to their minimum only"}}
 
 
 def run_bolt(args, world, rank, local):
     import torch
 
-    from paper_1706_10283_gb300 import bolt
+    from paper_1706_10283_gb300 import bolt, synth
     from paper_1706_10283_gb300.pipeline import SearchStep
 
     torch.cuda.set_device(local)
     bolt.lib()
     hbm_peak, peak_kind = peaks()
-    cfg = workload(args.nq)
-    n, J, M, nq, k = cfg["n"], cfg["J"], cfg["M"], cfg["nq"], cfg["k"]
-    X, Q, Xd, Qd, C, quant = prepare(cfg, data_seed=rank)
-    step = SearchStep(n, J, M, nq, k, C, quant, streams=args.topk_streams)
-    step.set_inputs(Xd, Qd)
+    cfg1 = workload(None)
+    X, Q1, Xd, Qd, C, quant = prepare(cfg1, data_seed=rank)
+    big = synth.CONFIGS["serve_50m"]
+    n, J, M, k, nq = big["n"], big["J"], big["M"], 100, args.large_nq
+    seed_base = 5000 + 100 * rank
+    codes50 = build_50m(C, seed_base)
+    row0, Xins = insert_batch(seed_base)
+    Q50 = synth.mixture(nq, J, 1)
+    step = SearchStep(n, J, M, nq, k, C, quant, streams=args.large_streams, codes=codes50, insert_row0=row0,
+                      insert_rows=Xins.shape[0])
+    step.set_inputs(Xins, torch.from_numpy(Q50).cuda())
     step.capture()
 
     # ---- device-resident timed region
@@ -658,15 +875,17 @@ def run_bolt(args, world, rank, local):
         step.replay(timed=True)
     ev1.record()
     torch.cuda.synchronize()
-    topk_ms = [step.topk_ms_per_launch()]
     clocks = sampler.stop()
     barrier(world)
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world)
+    per_query = step.topk_ms_per_launch()
+    for m in step.metrics:
+        bolt.check_topk(step.idx[m])
     value = world * 2.0 * nq * n / (ms * 1e-3)
 
     # ---- end to end from pinned host buffers
-    Xh = torch.from_numpy(X).pin_memory()
-    Qh = torch.from_numpy(Q).pin_memory()
+    Xh = Xins.cpu().pin_memory()
+    Qh = torch.from_numpy(Q50).pin_memory()
     oi = [torch.empty((nq, k), dtype=torch.int64).pin_memory() for _ in range(2)]
     od = [torch.empty((nq, k), dtype=torch.float32).pin_memory() for _ in range(2)]
     for _ in range(max(1, args.warmup)):
@@ -678,73 +897,56 @@ def run_bolt(args, world, rank, local):
         step.run_from_host(Xh, Qh, oi, od)
     ev1.record()
     torch.cuda.synchronize()
+    for t in oi:
+        bolt.check_topk(t)
     ems = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world)
     e2e = {"value": world * 2.0 * nq * n / (ems * 1e-3), "unit": UNIT, "ms_per_step": round(ems, 4),
            "h2d_bytes_per_step": step.h2d_bytes(), "d2h_bytes_per_step": step.d2h_bytes(),
            "api": "SearchStep.run_from_host (pinned host -> libbolt.so -> pinned host)"}
 
-    # ---- roofline of the dominant kernel (fused scan + top-k, L2-resident
-    # codes): one launch timed by itself (serial launches, graph replay)
-    tk_ms = float(np.median(topk_ms))
+    # ---- roofline of the dominant kernel: one launch by itself, and the
+    # bare lookup core over the same codes
     launch_ms = step.serial_topk_ms()
-    cold_ms = step.flushed_topk_ms()
-    lookups = n * M  # one table lookup + add per (vector, codebook) for one query
-    roof = roofline_topk(launch_ms, n, M, hbm_peak, peak_kind)
+    core_us = bolt.probe_lookup_core(codes50, n, step.luts[bolt.METRIC_L2][0].contiguous(), reps=10)
+    roof = roofline_topk_50m(launch_ms, n, M, hbm_peak, peak_kind, core_us)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": config_dict(cfg),
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": config_dict(args),
             "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps * step.launches_per_step,
             "gpu_launches_per_step": step.launches_per_step, "roofline": roof,
-            "topk_ms_per_launch": round(launch_ms, 5), "topk_ms_per_query_in_step": round(tk_ms, 5),
-            "topk_streams": len(step.side), "lookups_per_launch": lookups,
-            "topk_l2_flushed": {"ms_per_launch": round(cold_ms, 5),
-                                "code_GBps": round(n * M / 2 / (cold_ms * 1e-3) / 1e9, 1),
-                                "hbm_frac": round(n * M / 2 / (cold_ms * 1e-3) / 1e9 / hbm_peak, 4),
-                                "flush": "512 MB written before each launch (> 2x L2)"}}
+            "topk_ms_per_query_in_step": round(per_query, 5),
+            "code_GBps_in_step": round(2 * nq * n * M / 2 / (ms * 1e-3) / 1e9, 1)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import parallel
+
+        codes_host = bolt.unpack_codes(codes50, n, M).cpu().numpy()
+        Cn = C.cpu().numpy()
+        Xins_h = Xh.numpy()
+        v1, w1, d1 = oracle_step_sample(codes_host, Xins_h, Q50, Cn, quant, nq, k, threads=1, q_sample=1)
+        nt = parallel.host_threads()
+        vn, wn, dn = oracle_step_sample(codes_host, Xins_h, Q50, Cn, quant, nq, k, threads=nt, q_sample=4)
+        line["cpu_baseline"] = {"value": vn, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": dn,
+                                "cpu_seconds": round(wn, 2),
+                                "single_thread": {"value": v1, "cores": 1, "sample": d1,
+                                                  "cpu_seconds": round(w1, 2)}}
+        del codes_host
+    del step
+    torch.cuda.empty_cache()
     if rank == 0 and not args.no_aux:
-        del step
-        torch.cuda.empty_cache()
+        line["mixture_1m"] = one_million_step(args, X, Q1, Xd, Qd, C, quant, hbm_peak, peak_kind)
+        line["small_iid_l2"] = small_iid_step()
+        line["batch_64_on_50m"] = batch_64_on_50m(codes50, C, quant)
         line["accuracy_mixture_1m"] = accuracy_report(Xd, C, quant)
-        codes50 = build_50m(C)
-        line["large_n_scan"] = large_n_scan(codes50, C, quant, hbm_peak, peak_kind)
+        del Xd
         line["serving"] = serving(codes50, C, quant)
         del codes50
         torch.cuda.empty_cache()
         line["encode_10m"] = encode_10m()
         line["batched_collections"] = batched_collections()
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-
-        Cn = C.cpu().numpy()
-        v, work, desc = cpu_sample(cfg, X, Q, Cn, quant, rows_enc=cfg["n"], q_sample=200)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-                                "cpu_seconds": round(work, 2)}
-        del oracle
+        line["approx_matmul"] = approx_matmul_standalone(hbm_peak)
     if rank == 0:
         print(json.dumps(line), flush=True)
-
-
-def roofline_topk(tk_ms, n, M, hbm_peak, peak_kind, kernel="topk_small_kernel"):
-    """Roofline entry for the fused scan + top-k kernel (at 1M vectors the
-    library runs its shared-memory size class, topk_small_kernel).  In this
-    workload the 8 MB of codes stay in L2 across the 1,000 launches of a
-    step, so the kernel's bound is the integer pipe that executes the table
-    lookups; the algorithmic work per launch is n*M lookup-adds."""
-    from paper_1706_10283_gb300 import alu_peak
-
-    peak_lookups = alu_peak.lookups_per_s()
-    achieved = n * M / (tk_ms * 1e-3)
-    return {"bound": "alu", "kernel": kernel, "achieved": round(achieved / 1e12, 4),
-            "peak": round(peak_lookups / 1e12, 4), "unit": "Tlookup/s", "frac": round(achieved / peak_lookups, 4),
-            # dram__bytes_read + write of one launch in an ncu --set full
-            # capture of this kernel at this size (cold caches: the 8 MB of
-            # codes read once; warm, as in the step, they come from L2)
-            "traffic": 8082944, "traffic_unit": "bytes per launch", "algorithmic_bytes": n * M // 2,
-            "peak_source": alu_peak.SOURCE,
-            "one_query_per_pass_cap": round(alu_peak.lookups_per_s_one_query() / 1e12, 4),
-            "hbm_equivalent_GBps": round(n * M / 2 / (tk_ms * 1e-3) / 1e9, 1), "hbm_peak_GBps": hbm_peak,
-            "hbm_peak_kind": peak_kind}
 
 
 def run_only(args):
@@ -766,8 +968,18 @@ def run_only(args):
         X, Q, Xd, Qd, C, quant = prepare(cfg, 0)
         del X, Xd
         codes50 = build_50m(C)
-        hbm_peak, peak_kind = peaks()
-        print(json.dumps(large_n_scan(codes50, C, quant, hbm_peak, peak_kind)), flush=True)
+        n, M, k = 50_000_000, cfg["M"], 100
+        a, b = quant[bolt.METRIC_L2]
+        luts = bolt.build_luts(Qd[:8].contiguous(), C, bolt.METRIC_L2, a, b)
+        ws = torch.empty(bolt.topk_workspace_bytes(n, M, 1, k), dtype=torch.uint8, device="cuda")
+
+        def eight(s):
+            for i in range(8):
+                bolt.topk(codes50, n, M, luts[i:i + 1], k, bolt.METRIC_L2, workspace=ws, stream=s)
+
+        print(json.dumps({"topk_kernel_50m_ms_per_launch": round(_graph_ms(eight, reps=3) / 8, 4),
+                          "lookup_core_us": round(bolt.probe_lookup_core(codes50, n, luts[0].contiguous()), 2)}),
+              flush=True)
         return
     if args.only == "serve":
         cfg = workload(8)

@@ -350,6 +350,26 @@ int bolt_fit_quantizer(const float *Qtrain, int64_t nqt, int32_t J, int32_t M,
                        const float *centroids, int32_t metric, float *a_host,
                        float *b_host, int32_t *alpha_idx_host, void *stream);
 
+/* ---------------------------------------------------------------- measurement probes
+ * Roofline denominators for the scan, measured on the device that is
+ * current (the paper has no counterpart; these compute no Bolt result).
+ *
+ * bolt_probe_int_lanes: integer-ALU lanes per clock per SM, from clock64()
+ * around a loop of independent byte permutes (prmt, the scan's lookup
+ * instruction) on one CTA of 1024 threads per SM.  Synchronous; allocates
+ * and frees 264 bytes of device memory.
+ *
+ * bolt_probe_lookup_core: microseconds per pass of the scan's lookup core
+ * (M = 16, blocked layout, the streaming kernel's bulk-copy rings) over n
+ * vectors of codes with the 16 x 16 uint8 tables luts, keeping only the
+ * smallest sum: the time below which no one-query fused scan + top-k on
+ * this core can go.  codes and luts are device pointers, 16-byte aligned;
+ * reps timed passes after two warm-up passes, on `stream`, synchronized
+ * before return.  BOLT_ETIMEOUT if a bounded wait gave up. */
+int bolt_probe_int_lanes(double *lanes_per_clk_per_sm);
+int bolt_probe_lookup_core(const uint8_t *codes, int64_t n, const uint8_t *luts, int32_t reps,
+                           float *us_per_pass, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

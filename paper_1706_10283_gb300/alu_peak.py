@@ -13,20 +13,50 @@ lookup (1.5 for a kernel that scans one query per pass), and the peak is
 
     SMs x ALU lanes per SM per clock x maximum SM clock / 1
 
-with the lane count measured on a GB300 by a throughput loop of independent
-prmt / lop3 instructions (INT_LANES_PER_SM).
+with the SM count read from the device, the maximum SM clock from
+nvidia-smi (clocks.max.sm), and the lane rate measured on the device by
+bolt_probe_int_lanes (a loop of independent prmt instructions; 64 lanes per
+clock per SM on GB300, the rate at which ncu's ALU-pipe utilization of the
+lookup kernels reads 100%).
 """
-SMS = 152
-MAX_SM_CLOCK_HZ = 2.070e9
-INT_LANES_PER_SM = 64  # measured prmt / lop3 throughput per SM per clock
+import subprocess
+
 ALU_OPS_PER_LOOKUP = 1.0  # byte-permute lookup floor, selector preparation amortized
 ALU_OPS_PER_LOOKUP_ONE_QUERY = 1.5  # selector preparation paid for every lookup word
-SOURCE = ("152 SMs x %d int32 ALU lanes/clk x 2070 MHz / 1 ALU op per lookup (byte-permute floor; "
-          "one-query-per-pass kernels are capped at 2/3 of it)" % INT_LANES_PER_SM)
+
+_cache = {}
+
+
+def device_numbers():
+    """(SMs, maximum SM clock in Hz, ALU lanes per clock per SM, source text)."""
+    if "v" not in _cache:
+        import torch
+
+        from . import bolt
+
+        dev = torch.cuda.current_device()
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = None
+        try:
+            out = subprocess.run(["nvidia-smi", "-i", str(dev), "--query-gpu=clocks.max.sm",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+            mhz = float(out.stdout.strip().splitlines()[0])
+        except Exception:
+            mhz = None
+        clock_src = "nvidia-smi clocks.max.sm"
+        if not mhz:
+            mhz, clock_src = 2070.0, "GB300 maximum SM clock (nvidia-smi unavailable)"
+        lanes = bolt.probe_int_lanes()
+        src = ("%d SMs x %.1f int32 ALU lanes/clk (bolt_probe_int_lanes) x %.0f MHz (%s) / 1 ALU op per lookup "
+               "(byte-permute floor; one-query-per-pass kernels are capped at 2/3 of it)" % (sms, lanes, mhz,
+                                                                                            clock_src))
+        _cache["v"] = (sms, mhz * 1e6, lanes, src)
+    return _cache["v"]
 
 
 def int_ops_per_s():
-    return SMS * INT_LANES_PER_SM * MAX_SM_CLOCK_HZ
+    sms, hz, lanes, _ = device_numbers()
+    return sms * lanes * hz
 
 
 def lookups_per_s():
@@ -35,3 +65,7 @@ def lookups_per_s():
 
 def lookups_per_s_one_query():
     return int_ops_per_s() / ALU_OPS_PER_LOOKUP_ONE_QUERY
+
+
+def source():
+    return device_numbers()[3]

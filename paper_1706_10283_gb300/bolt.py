@@ -32,6 +32,9 @@ _lib = None
 
 _SIGS = {
     "bolt_last_error": ([], C.c_char_p),
+    "bolt_probe_int_lanes": ([C.POINTER(C.c_double)], C.c_int),
+    "bolt_probe_lookup_core": ([C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.POINTER(C.c_float), C.c_void_p],
+                               C.c_int),
     "bolt_version": ([], C.c_char_p),
     "bolt_codes_bytes": ([C.c_int64, C.c_int32], C.c_int64),
     "bolt_pack_codes": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
@@ -239,6 +242,25 @@ def scan_float(codes, n, M, luts_f32, out=None, stream=None):
         out = torch.empty((nq, n), dtype=torch.float32, device=luts_f32.device)
     _check(lib().bolt_scan_float(_ptr(codes), n, M, _ptr(luts_f32), nq, _ptr(out), _stream(stream)))
     return out
+
+
+def probe_int_lanes():
+    """Integer-ALU lanes per clock per SM of the current GPU (prmt loop)."""
+    v = C.c_double()
+    _check(lib().bolt_probe_int_lanes(C.byref(v)))
+    return v.value
+
+
+def probe_lookup_core(codes, n, luts, reps=10, stream=None):
+    """Microseconds per pass of the bare lookup core (M = 16) over n vectors
+    with one query's tables luts (16, 16) uint8: the floor of a one-query
+    fused scan + top-k."""
+    torch = _torch()
+    _dev(codes, torch.uint8, "codes")
+    _dev(luts, torch.uint8, "luts")
+    v = C.c_float()
+    _check(lib().bolt_probe_lookup_core(_ptr(codes), n, _ptr(luts), reps, C.byref(v), _stream(stream)))
+    return float(v.value)
 
 
 def topk_workspace_bytes(n, M, nq, k):

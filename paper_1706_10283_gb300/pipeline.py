@@ -2,7 +2,9 @@
 
 ``SearchStep`` owns device buffers for a database of n vectors and nq queries
 and runs, in order (all in libbolt.so kernels):
-  1. encode the database (Sec. 3.1 h, K = 16),
+  1. encode the database (Sec. 3.1 h, K = 16) -- or, for a resident database
+     passed in as ``codes``, encode a batch of ``insert_rows`` new vectors
+     into rows ``insert_row0 ..`` of it (an online insert, Sec. 1.3),
   2. build the uint8 query tables for each metric (Sec. 3.1 g, Sec. 3.2 beta),
   3. scan + exact top-k, one query per launch (the plain GPU form); the
      launches go round-robin to ``streams`` CUDA streams, each with its own
@@ -22,16 +24,31 @@ from . import bolt
 
 class SearchStep:
     def __init__(self, n, J, M, nq, k, centroids, quant, metrics=(bolt.METRIC_L2, bolt.METRIC_DOT),
-                 precision=bolt.PREC_FP32, device="cuda", streams=8):
+                 precision=bolt.PREC_FP32, device="cuda", streams=8, codes=None, insert_row0=0, insert_rows=None):
         self.n, self.J, self.M, self.nq, self.k = n, J, M, nq, k
         self.metrics = tuple(metrics)
         self.quant = dict(quant)  # metric -> (a, b)
         self.precision = precision
         dev = torch.device(device)
         self.C = centroids
-        self.X = torch.empty((n, J), dtype=torch.float32, device=dev)
+        nx = n if insert_rows is None else int(insert_rows)
+        r0 = int(insert_row0)
+        if r0 % 256 or r0 < 0 or r0 + nx > n or (r0 + nx != n and nx % 256):
+            raise ValueError("insert rows [%d, %d) must start on a 256-vector block and end on one or at n"
+                             % (r0, r0 + nx))
+        if codes is None and nx != n:
+            raise ValueError("an insert batch needs a resident database (codes)")
+        self.row0, self.nx = r0, nx
+        self.X = torch.empty((nx, J), dtype=torch.float32, device=dev)
         self.Q = torch.empty((nq, J), dtype=torch.float32, device=dev)
-        self.codes = torch.empty(bolt.codes_bytes(n, M), dtype=torch.uint8, device=dev)
+        if codes is None:
+            codes = torch.empty(bolt.codes_bytes(n, M), dtype=torch.uint8, device=dev)
+        if codes.numel() != bolt.codes_bytes(n, M):
+            raise ValueError("codes hold %d bytes, the layout of %d vectors needs %d"
+                             % (codes.numel(), n, bolt.codes_bytes(n, M)))
+        self.codes = codes
+        b0 = r0 // 256 * M * 128
+        self.codes_x = codes[b0:b0 + bolt.codes_bytes(nx, M)]  # the rows the step encodes
         self.luts = {m: torch.empty((nq, M, 16), dtype=torch.uint8, device=dev) for m in self.metrics}
         self.sums = {m: torch.empty((nq, k), dtype=torch.uint16, device=dev) for m in self.metrics}
         self.idx = {m: torch.empty((nq, k), dtype=torch.int64, device=dev) for m in self.metrics}
@@ -50,7 +67,7 @@ class SearchStep:
     # The step in three kinds of segments, so that top-k launches can be timed
     # by ordinary stream events recorded between graph replays.
     def _pre(self):
-        bolt.encode(self.X, self.C, self.precision, out=self.codes)
+        bolt.encode(self.X, self.C, self.precision, out=self.codes_x)
         for m in self.metrics:
             a, b = self.quant[m]
             bolt.build_luts(self.Q, self.C, m, a, b, out=self.luts[m])

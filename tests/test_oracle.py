@@ -536,3 +536,29 @@ def test_encode_and_tables_beyond_256_codebooks():
     L = oracle.quantize(D, a, bq)
     assert L.shape == (3, M, 16)
     np.testing.assert_array_equal(L, np.clip(np.floor(D * np.float32(a)), 0, 255).astype(np.uint8))
+
+
+@pytest.mark.parametrize("metric", [oracle.METRIC_L2, oracle.METRIC_DOT, oracle.METRIC_L1])
+def test_parallel_driver_equals_single_scan(metric):
+    """The threaded driver of the timed CPU baseline returns exactly the
+    oracle's single-threaded top-k, ties included (tables with 4 values make
+    long tie runs that cross range boundaries)."""
+    from oracle import parallel
+
+    rng = np.random.default_rng(30 + metric)
+    codes = rng.integers(0, 16, (100_003, 8)).astype(np.uint8)
+    luts = rng.integers(0, 4, (3, 8, 16)).astype(np.uint8)
+    want = oracle.topk(oracle.scan(codes, luts), 100, metric)
+    for threads in (1, 3, 7):
+        got = parallel.scan_topk(codes, luts, 100, metric, threads=threads)
+        np.testing.assert_array_equal(got[0], want[0])
+        np.testing.assert_array_equal(got[1], want[1])
+
+
+def test_parallel_encode_equals_encode():
+    from oracle import parallel
+
+    rng = np.random.default_rng(31)
+    X = rng.standard_normal((10_007, 16)).astype(np.float32)
+    C = rng.standard_normal((4, 16, 4)).astype(np.float32)
+    np.testing.assert_array_equal(parallel.encode(X, C, threads=3, chunk=1000), oracle.encode(X, C))
