@@ -63,6 +63,7 @@ def lib():
             "bo_dequant_u32": [u32p, i64, f32, f32, f32p],
             "bo_scan_float": [u8p, i64, i32, f32p, i64, f32p],
             "bo_topk": [u16p, i64, i64, i32, i32, u16p, i64p],
+            "bo_topk_u32": [u32p, i64, i64, i32, i32, u32p, i64p],
             "bo_dequant_params": [f32, f32p, i32, C.POINTER(C.c_float), C.POINTER(C.c_float)],
             "bo_dequant": [u16p, i64, f32, f32, f32p],
             "bo_matmul": [f32p, i64, i32, u8p, i64, i32, f32p, f32, f32p, f32p],
@@ -222,6 +223,17 @@ def topk(sums, k, metric):
     os_ = np.empty((nq, k), np.uint16)
     oi = np.empty((nq, k), np.int64)
     _ok(lib().bo_topk(sums, n, nq, k, metric, os_, oi), "topk")
+    return os_, oi
+
+
+def topk_u32(sums, k, metric):
+    """top-k over uint32 sums (more than 256 codebooks): (sums nq x k uint32,
+    idx nq x k int64), best first, ties to the lower index."""
+    sums = np.ascontiguousarray(sums, dtype=np.uint32)
+    nq, n = sums.shape
+    os_ = np.empty((nq, k), np.uint32)
+    oi = np.empty((nq, k), np.int64)
+    _ok(lib().bo_topk_u32(sums, n, nq, k, metric, os_, oi), "topk_u32")
     return os_, oi
 
 

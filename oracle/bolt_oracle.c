@@ -488,6 +488,43 @@ int bo_topk(const uint16_t *sums, int64_t n, int64_t nq, int32_t k, int32_t metr
     return BO_OK;
 }
 
+/* The same selection over the uint32 sums of more than 256 codebooks
+ * (bo_scan_u32): the order (L2 and L1 ascending, dot descending) and the tie
+ * rule (lower index first) are those of bo_topk. */
+static int better_u32(int32_t metric, uint32_t s1, int64_t i1, uint32_t s2, int64_t i2) {
+    if (s1 != s2) return metric == BO_METRIC_DOT ? s1 > s2 : s1 < s2;
+    return i1 < i2;
+}
+
+int bo_topk_u32(const uint32_t *sums, int64_t n, int64_t nq, int32_t k, int32_t metric,
+                uint32_t *out_sums, int64_t *out_idx) {
+    if (n < 0 || nq < 0 || k <= 0) return BO_EINVAL;
+    if (metric != BO_METRIC_L2 && metric != BO_METRIC_DOT && metric != BO_METRIC_L1) return BO_EINVAL;
+    for (int64_t q = 0; q < nq; q++) {
+        uint32_t *bs = out_sums + q * k;
+        int64_t *bi = out_idx + q * k;
+        int cnt = 0;
+        for (int64_t i = 0; i < n; i++) {
+            uint32_t s = sums[q * n + i];
+            if (cnt == k && !better_u32(metric, s, i, bs[k - 1], bi[k - 1])) continue;
+            int pos = cnt < k ? cnt : k - 1;
+            while (pos > 0 && better_u32(metric, s, i, bs[pos - 1], bi[pos - 1])) {
+                bs[pos] = bs[pos - 1];
+                bi[pos] = bi[pos - 1];
+                pos--;
+            }
+            bs[pos] = s;
+            bi[pos] = i;
+            if (cnt < k) cnt++;
+        }
+        for (int r = cnt; r < k; r++) {
+            bs[r] = 0;
+            bi[r] = -1;
+        }
+    }
+    return BO_OK;
+}
+
 /* ---------------------------------------------------------------- dequantize
  * Sec. 3.2: sum of per-table reconstructions beta_m/a + b_m = S/a + sum_m b_m;
  * the bias sum_m b_m is the "one overall bias" known after training. */

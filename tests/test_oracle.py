@@ -407,6 +407,24 @@ def test_topk_matches_lexsort(metric):
         np.testing.assert_array_equal(got_s[q], sums[q][order])
 
 
+@pytest.mark.parametrize("metric", [oracle.METRIC_L2, oracle.METRIC_DOT, oracle.METRIC_L1])
+def test_topk_u32_matches_lexsort(metric):
+    """The uint32-sum top-k (more than 256 codebooks) against numpy lexsort,
+    with sums past the uint16 range and long tie runs; ties to the lower
+    index, L2 / L1 ascending, dot descending."""
+    rng = np.random.default_rng(18)
+    sums = (rng.integers(0, 50, (3, 7000)) * 7919 + 60_000).astype(np.uint32)  # values up to ~450,000
+    for k in (1, 100, 1024):
+        got_s, got_i = oracle.topk_u32(sums, k, metric)
+        for q in range(3):
+            key = -sums[q].astype(np.int64) if metric == oracle.METRIC_DOT else sums[q].astype(np.int64)
+            order = np.lexsort((np.arange(7000), key))[:k]
+            np.testing.assert_array_equal(got_i[q], order)
+            np.testing.assert_array_equal(got_s[q], sums[q][order])
+    s, i = oracle.topk_u32(np.array([[70_000, 3, 70_000]], np.uint32), 5, oracle.METRIC_DOT)
+    assert i.tolist() == [[0, 2, 1, -1, -1]] and s.tolist() == [[70_000, 70_000, 3, 0, 0]]
+
+
 def test_topk_pads_when_k_exceeds_n():
     s, i = oracle.topk(np.array([[5, 3, 5]], np.uint16), 5, oracle.METRIC_L2)
     assert i.tolist() == [[1, 0, 2, -1, -1]] and s.tolist() == [[3, 5, 5, 0, 0]]
