@@ -27,7 +27,7 @@
 // therefore has D_k > D_best and cannot be the canonical argmin; the kernel
 // uses twice that margin.  When more than one centroid lies inside it, the
 // canonical fp32 distances of those candidates are recomputed from the fp32
-// inputs in shared memory and the smallest (lowest index on ties) wins.
+// inputs and the smallest (lowest index on ties) wins.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -41,10 +41,8 @@
 namespace bolt {
 
 constexpr int kTcRows = 128;      // vectors per tile: MMA M and TMEM lanes
-constexpr int kTcThreads = 128;   // thread r owns row r (TMEM lane r)
 constexpr int kTcKC = 32;         // dims per chunk: two K = 16 slices
 constexpr int kTcStageBytes = kTcRows * kTcKC * 4;  // one 128 x 32 fp32 chunk (TMA box), 16 KB
-constexpr int kTcStages = 2;                         // TMA ring depth
 constexpr uint64_t kTcWait = 1000000000ull;  // 1 s bound on every wait
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -75,17 +73,22 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
-// 16 consecutive fp32 columns of this thread's tensor-memory lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 16 consecutive fp32 columns of this thread's tensor-memory lane, without
+// waiting: the values are valid after tmem_wait_ld(v).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, float (&v)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),
+          "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+// Wait for this thread's tensor-memory loads; v is an operand so that no use
+// of the loaded registers is scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld(float (&v)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
+                   "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),
+                   "+f"(v[15]));
 }
 
 // Shared-memory matrix descriptor for a K-major operand without swizzle: the
@@ -123,59 +126,140 @@ __device__ __forceinline__ uint32_t swz_off(int r, int j) {
     return (uint32_t)(r * 128 + ((((j >> 2) ^ (r & 7))) << 4) + (j & 3) * 4);
 }
 
-// 2-D tiled TMA load of box (32 dims, 128 rows) at (x = dim, y = row).
+// ------------------------------------------------------------------ warp-specialized pipeline
+// Warp roles:
+//   warp 0        MMA issuer (one thread) and owner of the tensor memory
+//   warp 1        bulk-copy producer: 128 x 32 fp32 chunks into a ring of kWsX stages
+//   warps 2..5    converters, one row per thread: fp32 -> bf16 hi/lo tiles
+//                 (core-matrix layout) and the squared norm of every subspace
+//   warps 6..21   epilogue, four warps per tensor-memory lane quarter (warp
+//                 id mod 4), each with a share of the chunk's subspaces: scores
+//                 from tensor memory, argmin with the margin, fp32 re-check of
+//                 near ties (x read from global memory), codes
+// The roles run ahead of one another through rings of mbarriers:
+//   xfull/xfree   fp32 stage   (producer -> converters -> producer)
+//   afull/afree   bf16 tiles   (converters -> MMA -> converters)
+//   accfull/free  accumulators (MMA -> epilogue -> MMA), one tensor-memory
+//                 buffer of COLS columns per slot
+//   nfull/nfree   norms        (converters -> epilogue -> converters)
+// Every wait is bounded (1 s); a role that gives up sets the CTA's failure
+// flag, every other role leaves at its next wait, and the CTA waits (bounded)
+// for its own copies and MMAs in flight before freeing the tensor memory.
+// Ring depths: the bf16 tiles and the accumulators are held until the MMAs
+// that use them complete (about 2 us after issue), so both rings hold several
+// chunks; the fp32 stages cover the copy latency.
+constexpr int kWsWarps = 22;
+constexpr int kWsThreads = kWsWarps * 32;
+constexpr int kWsXMax = 6;  // staged fp32 chunks (as many as fit, at least 2)
+constexpr int kWsA = 4;     // converted bf16 chunks
+constexpr int kMmaWarp = 0, kProducerWarp = 1;
+constexpr int kConvWarp0 = 2, kConvWarps = 4, kEpiWarp0 = 6, kEpiWarps = 16, kEpiParts = kEpiWarps / 4;
+constexpr int kABytes = 2 * kTcRows * kTcKC * 2;  // hi tile + lo tile of one chunk, 16 KB
+constexpr int kMaxWsB = 8;
+constexpr size_t kWsSmemCap = 224 * 1024;
+// barrier slots
+constexpr int kBarXFull = 0, kBarXFree = kBarXFull + kWsXMax, kBarAFull = kBarXFree + kWsXMax,
+              kBarAFree = kBarAFull + kWsA, kBarAccFull = kBarAFree + kWsA, kBarAccFree = kBarAccFull + kMaxWsB,
+              kBarNFull = kBarAccFree + kMaxWsB, kBarNFree = kBarNFull + kMaxWsB, kBarCount = kBarNFree + kMaxWsB;
 
-// Canonical fp32 distance (the encoder's definition) of subvector (r, dims
-// j0..j0+s) of a staged chunk to one centroid c (s contiguous floats).
-__device__ __forceinline__ float canon_dist(const uint8_t *stage, int r, int j0, const float *__restrict__ c, int s) {
+template <int S>
+struct WsShape {
+    using SH = TcShape<S>;
+    static constexpr int NB = SH::COLS >= 128 ? 4 : 8;  // accumulator slots (at most 512 columns)
+    // subspaces of a chunk per epilogue part (SPC / kEpiParts, at least 1)
+    static constexpr int PER_PART = SH::SPC >= kEpiParts ? SH::SPC / kEpiParts : 1;
+    static constexpr int NCOLS_USED = NB * SH::COLS;
+    static constexpr int NCOL = NCOLS_USED < 32 ? 32 : NCOLS_USED;  // power of two
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// try_wait with a suspend-time hint: a waiting thread sleeps (up to 20 us)
+// until the phase completes instead of spinning on issue slots the other
+// roles of its scheduler need.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `par` of bar; false if it does not complete within kTcWait
+// (the failure flag is then set) or another role has already failed.
+__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t par, volatile uint32_t *fail) {
+    if (mbar_try_wait(bar, par)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait_sleep(bar, par)) {
+        if (*fail) return false;
+        if (globaltimer_ns() - t0 > kTcWait) {
+            *fail = 1u;
+            return false;
+        }
+    }
+    return true;
+}
+
+// Canonical fp32 distance of x's subvector (s contiguous floats in global
+// memory) to one centroid c.
+__device__ __forceinline__ float canon_dist_g(const float *__restrict__ x, const float *__restrict__ c, int s) {
     float acc = 0.0f;
     for (int j = 0; j < s; ++j) {
-        const float x = *reinterpret_cast<const float *>(stage + swz_off(r, j0 + j));
-        const float t = __fsub_rn(x, __ldg(c + j));
+        const float t = __fsub_rn(__ldg(x + j), __ldg(c + j));
         acc = __fmaf_rn(t, t, acc);
     }
     return acc;
 }
 
 template <int S>
-__global__ void __launch_bounds__(kTcThreads) encode_tc_kernel(const __grid_constant__ CUtensorMap xmap, int64_t n,
-                                                               int32_t J, int32_t M, const float *__restrict__ C,
-                                                               uint32_t *__restrict__ codes,
-                                                               unsigned long long *__restrict__ n_rechecked) {
+__global__ void __launch_bounds__(kWsThreads, 1)
+    encode_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float *__restrict__ Xg, int64_t n, int32_t J,
+                     int32_t M, const float *__restrict__ C, uint32_t *__restrict__ codes,
+                     unsigned long long *__restrict__ n_rechecked, int kWsX) {
     using SH = TcShape<S>;
+    using WS = WsShape<S>;
+    constexpr int NB = WS::NB;
     extern __shared__ __align__(1024) uint8_t tsm[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nslices = J / 16;
     const int nchunks = J / kTcKC;
 
-    // shared memory: fp32 staging x2 (1024-aligned, swizzled) | A tiles | B slices | norms | barriers
-    // the swizzled TMA destination must be 1024-byte aligned
+    // shared memory: fp32 stages (1024-aligned, swizzled) | bf16 A tiles | B slices | norms | ||c||^2 |
+    //                margin coefficients | barriers | slots
     uint8_t *p = tsm + ((1024u - (smem_u32(tsm) & 1023u)) & 1023u);
     uint8_t *X32 = p;
-    p += kTcStages * kTcStageBytes;
-    uint8_t *A = p;  // two buffers, each a hi tile then a lo tile
-    p += 2 * 2 * kTcRows * kTcKC * 2;  // 2 x 16 KB
+    p += kWsX * kTcStageBytes;
+    uint8_t *A = p;
+    p += kWsA * kABytes;
     uint8_t *B = p;  // hi slices, then lo slices
     p += 2 * (size_t)nslices * SH::SLICE_BYTES;
+    float *nrm = reinterpret_cast<float *>(p);  // [NB][SPC][128] squared subspace norms
+    p += (size_t)NB * SH::SPC * kTcRows * 4;
     float *cn2 = reinterpret_cast<float *>(p);  // [M][16] fp32 ||c_k||^2
     p += (size_t)M * kK * 4;
     float *cmax = reinterpret_cast<float *>(p);  // [M][4]: margin polynomial p0, p1, p2 (rounded up)
     p += (size_t)M * 4 * 4;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(p);  // [0..kTcStages): staging; [6], [7]: MMA buffers
-    p += 8 * 8;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(p);
+    p += kBarCount * 8;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(p);  // [0] TMEM base, [1] rechecks, [2] failure
+    volatile uint32_t *fail = tslot + 2;
 
-    // ---- one-time set-up: norms and the bf16 B slices
-    for (int mk = tid; mk < M * kK; mk += kTcThreads) {
+    // ---- one-time set-up: norms, margin coefficients and the bf16 B slices
+    for (int mk = tid; mk < M * kK; mk += kWsThreads) {
         const float *c = C + (size_t)mk * S;
         float acc = 0.0f;
         for (int j = 0; j < S; ++j) acc = __fmaf_rn(c[j], c[j], acc);
         cn2[mk] = acc;
     }
-    // Margin 4 (eps + eta) = p0 + p1 X + p2 X^2 per codebook, with
-    //   eps + eta = 2 E1 X C + U (C2 + 2 X C) + U (X + C)^2
-    // (C = max_k ||c_k||, C2 = max_k ||c_k||^2, computed in fp64 and rounded up).
-    for (int m = tid; m < M; m += kTcThreads) {
+    // Margin 4 (eps + eta) = p0 + p1 X + p2 X^2 per codebook (kernel header),
+    // with C = max_k ||c_k|| and C2 = max_k ||c_k||^2 in fp64, rounded up.
+    for (int m = tid; m < M; m += kWsThreads) {
         double mx = 0.0, mx2 = 0.0;
         for (int k = 0; k < kK; ++k) {
             double d2 = 0.0;
@@ -197,32 +281,43 @@ __global__ void __launch_bounds__(kTcThreads) encode_tc_kernel(const __grid_cons
         cmax[4 * m + 2] = (float)(p2 * (1.0 + 1e-6));
         cmax[4 * m + 3] = 0.0f;
     }
-    for (int e = tid; e < nslices * SH::NS * 16; e += kTcThreads) {
-        const int T = e / (SH::NS * 16), n = (e / 16) % SH::NS, k = e % 16;
+    for (int e = tid; e < nslices * SH::NS * 16; e += kWsThreads) {
+        const int T = e / (SH::NS * 16), nn = (e / 16) % SH::NS, k = e % 16;
         float v;
         if (S <= 16) {
-            const int m = T * (16 / S) + n / 16, kk = n % 16, d = k - S * (n / 16);
+            const int m = T * (16 / S) + nn / 16, kk = nn % 16, d = k - S * (nn / 16);
             v = (d >= 0 && d < S) ? C[((size_t)m * kK + kk) * S + d] : 0.0f;
         } else {
             const int m = (16 * T) / S, d0 = 16 * T - m * S;
-            v = C[((size_t)m * kK + n) * S + d0 + k];
+            v = C[((size_t)m * kK + nn) * S + d0 + k];
         }
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        *reinterpret_cast<__nv_bfloat16 *>(B + (size_t)T * SH::SLICE_BYTES + core_off(n, k, SH::NS)) = hi;
-        *reinterpret_cast<__nv_bfloat16 *>(B + (size_t)(nslices + T) * SH::SLICE_BYTES + core_off(n, k, SH::NS)) = lo;
+        *reinterpret_cast<__nv_bfloat16 *>(B + (size_t)T * SH::SLICE_BYTES + core_off(nn, k, SH::NS)) = hi;
+        *reinterpret_cast<__nv_bfloat16 *>(B + (size_t)(nslices + T) * SH::SLICE_BYTES + core_off(nn, k, SH::NS)) = lo;
     }
     if (tid == 0) {
-        for (int i = 0; i < kTcStages; ++i) mbar_init(&bars[i], 1);
-        mbar_init(&bars[6], 1);
-        mbar_init(&bars[7], 1);
+        for (int i = 0; i < kWsXMax; ++i) {
+            mbar_init(&bars[kBarXFull + i], 1);
+            mbar_init(&bars[kBarXFree + i], kConvWarps);
+        }
+        for (int i = 0; i < kWsA; ++i) {
+            mbar_init(&bars[kBarAFull + i], kConvWarps);
+            mbar_init(&bars[kBarAFree + i], 1);
+        }
+        for (int i = 0; i < kMaxWsB; ++i) {
+            mbar_init(&bars[kBarAccFull + i], 1);
+            mbar_init(&bars[kBarAccFree + i], kEpiWarps);
+            mbar_init(&bars[kBarNFull + i], kConvWarps);
+            mbar_init(&bars[kBarNFree + i], kEpiWarps);
+        }
         tslot[1] = 0;
         tslot[2] = 0;
     }
     fence_mbar_init();
     fence_proxy_async_smem();  // B written by threads, read by the tensor cores
-    if (warp == 0) {
-        tmem_alloc(&tslot[0], SH::NCOL);
+    if (warp == kMmaWarp) {
+        tmem_alloc(&tslot[0], WS::NCOL);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -231,71 +326,42 @@ __global__ void __launch_bounds__(kTcThreads) encode_tc_kernel(const __grid_cons
     const uint32_t tmem = tslot[0];
 
     const int64_t ntiles = (n + kTcRows - 1) / kTcRows;
-    constexpr uint32_t kIdesc = idesc_bf16_f32(kTcRows, SH::NS);
-    const uint32_t a_addr = smem_u32(A), b_addr = smem_u32(B);
-
-    // This CTA's chunks in order: q -> tile blockIdx.x + (q / nchunks) * gridDim.x,
-    // dims (q % nchunks) * 32.  Chunk q is staged in ring slot q % kTcStages,
-    // converted into A buffer q % 2 and multiplied into TMEM buffer q % 2.
+    // This CTA's chunks in order: q -> tile blockIdx.x + (q / nchunks) * gridDim.x, dims (q % nchunks) * 32.
     const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const uint32_t total = (uint32_t)(my_tiles * nchunks);
     auto q_tile = [&](uint32_t q) -> int64_t { return blockIdx.x + (int64_t)(q / nchunks) * gridDim.x; };
-    auto stage = [&](uint32_t q) {  // one TMA per chunk; rows past n read as zeros
-        if (tid == 0 && q < total) {
-            const int sl = (int)(q % kTcStages);
-            mbar_arrive_expect_tx(&bars[sl], (uint32_t)kTcStageBytes);
-            tma_load_2d(X32 + (size_t)sl * kTcStageBytes, &xmap, (int)(q % nchunks) * kTcKC,
-                        (int)(q_tile(q) * kTcRows), &bars[sl]);
-        }
-    };
-    for (uint32_t q = 0; q < kTcStages; ++q) stage(q);  // fill the ring; slot q % kTcStages is refilled
-                                                         // with chunk q + kTcStages after chunk q's epilogue
-
-    bool failed = false;
     unsigned my_rechecks = 0;
-    float xn_prev[SH::SPC];
-#pragma unroll
-    for (int i = 0; i < SH::SPC; ++i) xn_prev[i] = 0.0f;
-    for (uint32_t g = 0; g <= total; ++g) {
-        float xn[SH::SPC];
-#pragma unroll
-        for (int i = 0; i < SH::SPC; ++i) xn[i] = 0.0f;
-        if (g < total) {
-            // ---- chunk g: fp32 -> bf16 hi/lo A tiles and subspace norms; MMAs
-            const int sl = (int)(g % kTcStages);
-            const bool ok_x = mbar_wait_bounded(&bars[sl], (g / kTcStages) & 1u, kTcWait);
-            if (__syncthreads_or(!ok_x)) {
-                failed = true;
-                break;
+
+    if (warp == kProducerWarp) {
+        // ---------------- producer
+        if (lane == 0) {
+            uint32_t q = 0;
+            for (; q < total; ++q) {
+                const uint32_t xs = q % kWsX;
+                if (q >= kWsX && !ws_wait(&bars[kBarXFree + xs], ((q / kWsX) - 1) & 1u, fail)) break;
+                mbar_arrive_expect_tx(&bars[kBarXFull + xs], (uint32_t)kTcStageBytes);
+                tma_load_2d(X32 + (size_t)xs * kTcStageBytes, &xmap, (int)(q % nchunks) * kTcKC,
+                            (int)(q_tile(q) * kTcRows), &bars[kBarXFull + xs]);
             }
-            const uint8_t *xs_stage = X32 + (size_t)sl * kTcStageBytes;
-            uint8_t *Ab = A + (size_t)(g & 1u) * (2 * kTcRows * kTcKC * 2);
-#pragma unroll
-            for (int kc = 0; kc < kTcKC / 8; ++kc) {
-                const float4 lo = *reinterpret_cast<const float4 *>(xs_stage + swz_off(tid, 8 * kc));
-                const float4 hi = *reinterpret_cast<const float4 *>(xs_stage + swz_off(tid, 8 * kc + 4));
-                const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-                __nv_bfloat162 h[4], l[4];
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    h[qq] = __floats2bfloat162_rn(v[2 * qq], v[2 * qq + 1]);
-                    const float2 hf = __bfloat1622float2(h[qq]);
-                    l[qq] = __floats2bfloat162_rn(v[2 * qq] - hf.x, v[2 * qq + 1] - hf.y);
-                }
-                *reinterpret_cast<uint4 *>(Ab + core_off(tid, 8 * kc, kTcRows)) = *reinterpret_cast<const uint4 *>(h);
-                *reinterpret_cast<uint4 *>(Ab + kTcRows * kTcKC * 2 + core_off(tid, 8 * kc, kTcRows)) =
-                    *reinterpret_cast<const uint4 *>(l);
-#pragma unroll
-                for (int qq = 0; qq < 8; ++qq) xn[(8 * kc + qq) / S] = __fmaf_rn(v[qq], v[qq], xn[(8 * kc + qq) / S]);
-            }
-            fence_proxy_async_smem();
-            tc_fence_before();
-            __syncthreads();
-            if (tid == 0) {
+            // copies issued but perhaps not consumed (after a failure): let them land
+            if (*fail)
+                for (uint32_t j = (q > kWsX ? q - kWsX : 0); j < q; ++j)
+                    mbar_wait_bounded(&bars[kBarXFull + j % kWsX], (j / kWsX) & 1u, kTcWait / 10);
+        }
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t kIdesc = idesc_bf16_f32(kTcRows, SH::NS);
+            const uint32_t a_addr = smem_u32(A), b_addr = smem_u32(B);
+            uint32_t q = 0;
+            for (; q < total; ++q) {
+                const uint32_t a = q % kWsA, bb = q % NB;
+                if (!ws_wait(&bars[kBarAFull + a], (q / kWsA) & 1u, fail)) break;
+                if (q >= (uint32_t)NB && !ws_wait(&bars[kBarAccFree + bb], ((q / NB) - 1) & 1u, fail)) break;
                 tc_fence_after();
-                const int c = (int)(g % nchunks);
-                const uint32_t a_base = a_addr + (g & 1u) * (2 * kTcRows * kTcKC * 2);
-                const uint32_t d_base = tmem + (g & 1u) * SH::COLS;
+                const int c = (int)(q % nchunks);
+                const uint32_t a_base = a_addr + a * kABytes;
+                const uint32_t d_base = tmem + bb * SH::COLS;
 #pragma unroll
                 for (int tl = 0; tl < 2; ++tl) {
                     const int T = c * 2 + tl;
@@ -309,102 +375,175 @@ __global__ void __launch_bounds__(kTcThreads) encode_tc_kernel(const __grid_cons
                     tc_mma(d_base + dcol, ah, bl, kIdesc, 1u);
                     tc_mma(d_base + dcol, al, bh, kIdesc, 1u);
                 }
-                tc_commit(&bars[6 + (g & 1u)]);
+                tc_commit(&bars[kBarAFree + a]);
+                tc_commit(&bars[kBarAccFull + bb]);
+            }
+            // MMAs still in flight after a failure: let them finish before the tensor memory is freed
+            if (*fail && q > 0) mbar_wait_bounded(&bars[kBarAccFull + (q - 1) % NB], ((q - 1) / NB) & 1u, kTcWait / 10);
+        }
+    } else if (warp < kEpiWarp0) {
+        // ---------------- converters
+        const int r = (warp - kConvWarp0) * 32 + lane;
+        for (uint32_t q = 0; q < total; ++q) {
+            const uint32_t xs = q % kWsX, a = q % kWsA, bb = q % NB;
+            bool ok = ws_wait(&bars[kBarXFull + xs], (q / kWsX) & 1u, fail);
+            if (ok && q >= kWsA) ok = ws_wait(&bars[kBarAFree + a], ((q / kWsA) - 1) & 1u, fail);
+            if (ok && q >= (uint32_t)NB) ok = ws_wait(&bars[kBarNFree + bb], ((q / NB) - 1) & 1u, fail);
+            if (!__all_sync(0xFFFFFFFFu, ok)) break;
+            const uint8_t *xs_stage = X32 + (size_t)xs * kTcStageBytes;
+            uint8_t *Ab = A + (size_t)a * kABytes;
+            float xn[SH::SPC];
+#pragma unroll
+            for (int i = 0; i < SH::SPC; ++i) xn[i] = 0.0f;
+#pragma unroll
+            for (int kc = 0; kc < kTcKC / 8; ++kc) {
+                const float4 lo = *reinterpret_cast<const float4 *>(xs_stage + swz_off(r, 8 * kc));
+                const float4 hi = *reinterpret_cast<const float4 *>(xs_stage + swz_off(r, 8 * kc + 4));
+                const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+                __nv_bfloat162 h[4], l[4];
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    h[qq] = __floats2bfloat162_rn(v[2 * qq], v[2 * qq + 1]);
+                    const float2 hf = __bfloat1622float2(h[qq]);
+                    l[qq] = __floats2bfloat162_rn(v[2 * qq] - hf.x, v[2 * qq + 1] - hf.y);
+                }
+                *reinterpret_cast<uint4 *>(Ab + core_off(r, 8 * kc, kTcRows)) = *reinterpret_cast<const uint4 *>(h);
+                *reinterpret_cast<uint4 *>(Ab + kTcRows * kTcKC * 2 + core_off(r, 8 * kc, kTcRows)) =
+                    *reinterpret_cast<const uint4 *>(l);
+#pragma unroll
+                for (int qq = 0; qq < 8; ++qq) xn[(8 * kc + qq) / S] = __fmaf_rn(v[qq], v[qq], xn[(8 * kc + qq) / S]);
+            }
+#pragma unroll
+            for (int i = 0; i < SH::SPC; ++i) nrm[((size_t)bb * SH::SPC + i) * kTcRows + r] = xn[i];
+            fence_proxy_async_smem();  // this thread's A tiles, for the tensor cores
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&bars[kBarAFull + a]);
+                mbar_arrive(&bars[kBarXFree + xs]);
+                mbar_arrive(&bars[kBarNFull + bb]);
             }
         }
-        if (g >= 1) {
-            // ---- epilogue of chunk g-1 (its MMAs ran while chunk g was converted)
-            const uint32_t e = g - 1;
-            const bool ok_m = mbar_wait_bounded(&bars[6 + (e & 1u)], (e >> 1) & 1u, kTcWait);
-            if (__syncthreads_or(!ok_m)) {
-                failed = true;
-                break;
+    } else {
+        // ---------------- epilogue
+        const int ew = warp - kEpiWarp0, lq = warp & 3, part = ew / 4;
+        const bool pad_writer = ew == 0;  // writes the padding codes of the last block
+        const int r = lq * 32 + lane;  // this warp's tensor-memory lanes
+        constexpr int PP = WS::PER_PART;
+        constexpr int QB = 1;  // chunks per iteration
+        const int i0 = part * PP;            // this part's first subspace of a chunk
+        const bool has_work = i0 < SH::SPC;
+        for (uint32_t q0 = 0; q0 < total; q0 += QB) {
+            const uint32_t nq = min((uint32_t)QB, total - q0);
+            bool ok = true;
+            for (uint32_t j = 0; j < nq; ++j) {
+                const uint32_t q = q0 + j, bb = q % NB;
+                if (ok) ok = ws_wait(&bars[kBarAccFull + bb], (q / NB) & 1u, fail);
+                if (ok) ok = ws_wait(&bars[kBarNFull + bb], (q / NB) & 1u, fail);
             }
+            if (!__all_sync(0xFFFFFFFFu, ok)) break;
             tc_fence_after();
-            const int64_t t = q_tile(e);
-            const int c = (int)(e % nchunks);
-            const uint8_t *xs_stage = X32 + (size_t)(e % kTcStages) * kTcStageBytes;
-            const int64_t v = t * kTcRows + tid;
-            const bool valid = v < n;
+            if (has_work) {
+                // this part's accumulator columns of the nq chunks: all loads before the waits
+                float d[QB][PP][16];
 #pragma unroll
-            for (int i = 0; i < SH::SPC; ++i) {
-                const int m = c * SH::SPC + i;
-                float d[16];
-                tmem_ld16(tmem + (e & 1u) * SH::COLS + ((uint32_t)(warp * 32) << 16) + (uint32_t)(i * 16), d);
-                const float4 *c2 = reinterpret_cast<const float4 *>(cn2 + m * kK);
-                float sc[16];
+                for (int j = 0; j < QB; ++j)
 #pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) {
-                    const float4 cc = c2[k4];
-                    sc[4 * k4 + 0] = __fmaf_rn(-2.0f, d[4 * k4 + 0], cc.x);
-                    sc[4 * k4 + 1] = __fmaf_rn(-2.0f, d[4 * k4 + 1], cc.y);
-                    sc[4 * k4 + 2] = __fmaf_rn(-2.0f, d[4 * k4 + 2], cc.z);
-                    sc[4 * k4 + 3] = __fmaf_rn(-2.0f, d[4 * k4 + 3], cc.w);
-                }
-                float best = sc[0];
+                    for (int ii = 0; ii < PP; ++ii)
+                        if ((uint32_t)j < nq)
+                            tmem_ld16_nowait(tmem + ((q0 + j) % NB) * SH::COLS + ((uint32_t)(lq * 32) << 16) +
+                                                 (uint32_t)((i0 + ii) * 16),
+                                             d[j][ii]);
 #pragma unroll
-                for (int k = 1; k < 16; ++k) best = fminf(best, sc[k]);
-                // margin 4 (eps + eta) as a quadratic in X with per-codebook coefficients
-                const float Xn = sqrtf(xn_prev[i]) * 1.0001f + 1e-30f;
-                const float4 pc = reinterpret_cast<const float4 *>(cmax)[m];
-                const float lim = best + __fmaf_rn(__fmaf_rn(pc.z, Xn, pc.y), Xn, pc.x);
-                uint32_t mask = 0;
+                for (int j = 0; j < QB; ++j)
 #pragma unroll
-                for (int k = 0; k < 16; ++k) mask |= (sc[k] <= lim ? 1u : 0u) << k;
-                if (!(lim < INFINITY)) mask = 0xFFFFu;  // non-finite scores: check every centroid
-                // a unique candidate is the tensor-core minimum itself
-                uint32_t code = (uint32_t)(__ffs(mask) - 1) & 15u;
-                if (__popc(mask) > 1) {
-                    float bd = INFINITY;
-                    code = 0;
-                    for (int k = 0; k < 16; ++k) {
-                        if (!(mask & (1u << k))) continue;
-                        const float dk = canon_dist(xs_stage, tid, i * S, C + ((size_t)m * kK + k) * S, S);
-                        if (dk < bd) {
-                            bd = dk;
-                            code = (uint32_t)k;
+                    for (int ii = 0; ii < PP; ++ii) tmem_wait_ld(d[j][ii]);
+#pragma unroll
+                for (int j = 0; j < QB; ++j) {
+                    if ((uint32_t)j >= nq) break;
+                    const uint32_t q = q0 + j, bb = q % NB;
+                    const int64_t t = q_tile(q);
+                    const int c = (int)(q % nchunks);
+                    const int64_t v = t * kTcRows + r;
+                    const bool valid = v < n;
+#pragma unroll
+                    for (int ii = 0; ii < PP; ++ii) {
+                        const int i = i0 + ii;
+                        const int m = c * SH::SPC + i;
+                        const float4 *c2 = reinterpret_cast<const float4 *>(cn2 + m * kK);
+                        float sc[16];
+#pragma unroll
+                        for (int k4 = 0; k4 < 4; ++k4) {
+                            const float4 cc = c2[k4];
+                            sc[4 * k4 + 0] = __fmaf_rn(-2.0f, d[j][ii][4 * k4 + 0], cc.x);
+                            sc[4 * k4 + 1] = __fmaf_rn(-2.0f, d[j][ii][4 * k4 + 1], cc.y);
+                            sc[4 * k4 + 2] = __fmaf_rn(-2.0f, d[j][ii][4 * k4 + 2], cc.z);
+                            sc[4 * k4 + 3] = __fmaf_rn(-2.0f, d[j][ii][4 * k4 + 3], cc.w);
                         }
+                        float best = sc[0];
+#pragma unroll
+                        for (int k = 1; k < 16; ++k) best = fminf(best, sc[k]);
+                        // margin 4 (eps + eta) as a quadratic in X with per-codebook coefficients
+                        const float Xn = sqrtf(nrm[((size_t)bb * SH::SPC + i) * kTcRows + r]) * 1.0001f + 1e-30f;
+                        const float4 pc = reinterpret_cast<const float4 *>(cmax)[m];
+                        const float lim = best + __fmaf_rn(__fmaf_rn(pc.z, Xn, pc.y), Xn, pc.x);
+                        uint32_t mask = 0;
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) mask |= (sc[k] <= lim ? 1u : 0u) << k;
+                        if (!(lim < INFINITY)) mask = 0xFFFFu;  // non-finite scores: check every centroid
+                        // a unique candidate is the tensor-core minimum itself
+                        uint32_t code = (uint32_t)(__ffs(mask) - 1) & 15u;
+                        if (__popc(mask) > 1 && valid) {
+                            const float *xv = Xg + v * J + (int64_t)m * S;
+                            float bd = INFINITY;
+                            code = 0;
+                            for (int k = 0; k < 16; ++k) {
+                                if (!(mask & (1u << k))) continue;
+                                const float dk = canon_dist_g(xv, C + ((size_t)m * kK + k) * S, S);
+                                if (dk < bd) {
+                                    bd = dk;
+                                    code = (uint32_t)k;
+                                }
+                            }
+                            ++my_rechecks;
+                        }
+                        if (!valid) code = 0;
+                        uint32_t word = code << (4 * (lane & 7));
+                        word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
+                        word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
+                        word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
+                        if ((lane & 7) == 0) codes[((v >> 8) * M + m) * kRowWords + ((v & 255) >> 3)] = word;
                     }
-                    if (valid) ++my_rechecks;
                 }
-                if (!valid) code = 0;
-                uint32_t word = code << (4 * (lane & 7));
-                word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
-                word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
-                word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
-                if ((lane & 7) == 0) codes[((v >> 8) * M + m) * kRowWords + ((v & 255) >> 3)] = word;
-            }
-            if (t == ntiles - 1 && c == nchunks - 1 && ((t + 1) * kTcRows) % kBlockVecs != 0) {
-                // second half of the last block holds padding vectors: code 0
-                const int64_t blk = (t * kTcRows) >> 8;
-                for (int ee = tid; ee < M * 16; ee += kTcThreads)
-                    codes[(blk * M + ee / 16) * kRowWords + 16 + (ee % 16)] = 0u;
             }
             tc_fence_before();
-            __syncthreads();  // TMEM buffer e % 2 and ring slot e % kTcStages are free again
-            stage(e + kTcStages);
+            __syncwarp();
+            for (uint32_t j = 0; j < nq; ++j) {
+                const uint32_t q = q0 + j, bb = q % NB;
+                if (lane == 0) {
+                    mbar_arrive(&bars[kBarAccFree + bb]);
+                    mbar_arrive(&bars[kBarNFree + bb]);
+                }
+                const int64_t t = q_tile(q);
+                const int c = (int)(q % nchunks);
+                if (pad_writer && t == ntiles - 1 && c == nchunks - 1 && ((t + 1) * kTcRows) % kBlockVecs != 0) {
+                    // second half of the last block holds padding vectors: code 0
+                    const int64_t blk = (t * kTcRows) >> 8;
+                    for (int ee = lane; ee < M * 16; ee += 32)
+                        codes[(blk * M + ee / 16) * kRowWords + 16 + (ee % 16)] = 0u;
+                }
+            }
         }
-#pragma unroll
-        for (int i = 0; i < SH::SPC; ++i) xn_prev[i] = xn[i];
     }
-    // Leave cleanly: wait (bounded) for copies in flight, free tensor memory.
-    if (failed) {
-        // give copies and MMAs still in flight a bounded chance to land before
-        // the shared and tensor memory go away
-        const uint64_t t0 = globaltimer_ns();
-        while (globaltimer_ns() - t0 < kTcWait / 10) {
-        }
-        if (tid == 0) tslot[2] = 1;
-    }
+
     if (my_rechecks) atomicAdd(&tslot[1], my_rechecks);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         tc_fence_after();
-        tmem_dealloc(tmem, SH::NCOL);
+        tmem_dealloc(tmem, WS::NCOL);
     }
     if (tid == 0 && n_rechecked) {
-        if (tslot[2]) atomicExch(n_rechecked, ~0ull);  // -1: a wait gave up
+        if (*fail) atomicExch(n_rechecked, ~0ull);  // -1: a wait gave up
         else if (tslot[1]) atomicAdd(n_rechecked, (unsigned long long)tslot[1]);
     }
 }
@@ -432,27 +571,35 @@ template <int S>
 static int launch_tc(const float *X, int64_t n, int32_t J, int32_t M, const float *C, uint8_t *codes,
                      int64_t *n_rechecked, cudaStream_t stream) {
     using SH = TcShape<S>;
+    using WS = WsShape<S>;
     const int nslices = J / 16;
-    const size_t smem = 1024 + kTcStages * (size_t)kTcStageBytes + 2 * 2 * (size_t)kTcRows * kTcKC * 2 +
-                        2 * (size_t)nslices * SH::SLICE_BYTES + (size_t)M * kK * 4 + (size_t)M * 4 * 4 + 8 * 8 + 16;
-    if (smem > 200 * 1024) return launch_encode_fp32(X, n, J, M, C, codes, stream);
+    const size_t fixed = 1024 + kWsA * (size_t)kABytes + 2 * (size_t)nslices * SH::SLICE_BYTES +
+                         (size_t)WS::NB * SH::SPC * kTcRows * 4 + (size_t)M * kK * 4 + (size_t)M * 4 * 4 +
+                         kBarCount * 8 + 16;
+    // fp32 stages: enough bulk copies in flight to cover the memory latency
+    // (up to kWsXMax), within kWsSmemCap of shared memory; at least two
+    int nx = kWsXMax;
+    while (nx > 2 && fixed + (size_t)nx * kTcStageBytes > kWsSmemCap) --nx;
+    const size_t smem = fixed + (size_t)nx * kTcStageBytes;
+    if (smem > kWsSmemCap) return launch_encode_fp32(X, n, J, M, C, codes, stream);
     auto kern = encode_tc_kernel<S>;
     int rc = ensure_smem((const void *)kern, smem);
     if (rc) return rc;
     const int64_t ntiles = (n + kTcRows - 1) / kTcRows;
-    // at most 512 / NCOL CTAs may hold tensor memory on one SM at a time;
-    // shared memory keeps the resident CTAs per SM within that
+    // CTAs per SM: shared memory, the threads of an SM, and at most 512 / NCOL
+    // CTAs holding tensor memory at a time
     int per_sm = (int)((227 * 1024) / (smem + 1024));
+    if (per_sm > 2048 / kWsThreads) per_sm = 2048 / kWsThreads;
+    if (per_sm > 512 / WS::NCOL) per_sm = 512 / WS::NCOL;
     if (per_sm < 1) per_sm = 1;
-    if (per_sm > 512 / SH::NCOL) per_sm = 512 / SH::NCOL;
     int64_t grid = ntiles;
     const int64_t cap = (int64_t)device_sm_count() * per_sm;
     if (cap > 0 && grid > cap) grid = cap;
     CUtensorMap map;
     rc = make_x_map(X, n, J, &map);
     if (rc) return rc;
-    kern<<<(int)grid, kTcThreads, smem, stream>>>(map, n, J, M, C, reinterpret_cast<uint32_t *>(codes),
-                                                  reinterpret_cast<unsigned long long *>(n_rechecked));
+    kern<<<(int)grid, kWsThreads, smem, stream>>>(map, X, n, J, M, C, reinterpret_cast<uint32_t *>(codes),
+                                                  reinterpret_cast<unsigned long long *>(n_rechecked), nx);
     return check_launch("encode_tc_kernel");
 }
 

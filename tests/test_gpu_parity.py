@@ -345,6 +345,26 @@ def test_kmeans_matches_oracle(torch_cuda, n, J, M, iters):
     assert abs(obj_g - obj[-1]) <= 1e-5 * obj[-1]
 
 
+def test_kmeans_million_rows_matches_oracle(torch_cuda):
+    """k-means at scale: 1,000,000 x 128 mixture rows, M = 16, 4 Lloyd
+    iterations from the seeded init (Sec. 3.1 background).  The GPU sums the
+    fp64 centroid means over 489 fixed chunks of 2,048 rows, the oracle in
+    row order: centroids within rtol 1e-5 and the objective of the GPU
+    centroids within 1e-5 of the oracle's."""
+    torch = torch_cuda
+    n, J, M, iters = 1_000_000, 128, 16, 4
+    X = synth.mixture(n, J, 4)
+    rows = synth.kmeans_init_rows(n, 4)
+    got = bolt.fit_codebooks(dev(torch, X), M, iters, rows).cpu().numpy()
+    ref, obj = oracle.kmeans(X, M, iters, rows, return_objective=True)
+    np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-6)
+    from oracle import parallel
+
+    xh = oracle.decode(parallel.encode(X, got), got).astype(np.float64)
+    obj_g = ((X.astype(np.float64) - xh) ** 2).sum()
+    assert abs(obj_g - obj[-1]) <= 1e-5 * obj[-1]
+
+
 @pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
 def test_fit_quantizer_matches_oracle(torch_cuda, metric):
     torch = torch_cuda
@@ -522,6 +542,47 @@ def test_scan_u32_bitexact(torch_cuda, n, M):
         np.testing.assert_array_equal(bolt.scan_l2(blocked, n, M, L).cpu().numpy(), want.astype(np.uint16))
     b = rng.standard_normal(M).astype(np.float32)
     np.testing.assert_array_equal(bolt.dequantize_u32(got, 0.37, b).cpu().numpy(), oracle.dequant_u32(want, 0.37, b))
+
+
+@pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT, bolt.METRIC_L1])
+@pytest.mark.parametrize("n,M,k,nq,hi", [(1, 257, 1, 1, 256), (5, 300, 10, 2, 256), (20_003, 257, 100, 3, 256),
+                                          (70_001, 512, 1024, 2, 256), (300_001, 512, 100, 2, 256),
+                                          (4_100, 4096, 1, 2, 256), (50_000, 512, 100, 2, 2),
+                                          (40_000, 300, 64, 2, 1)])
+def test_topk_u32_bitexact(torch_cuda, metric, n, M, k, nq, hi):
+    """Fused top-k over uint32 sums for more than 256 codebooks (M up to
+    4096) against the oracle's selection over its own uint32 scan: ragged
+    n, k > n (padding), k = 1 and 1024, tables drawn from [0, hi) -- hi = 2
+    makes long tie runs at the k-th sum, hi = 1 makes every sum equal (the
+    first k indices) -- and the dot order; the sums exceed 65,535."""
+    torch = torch_cuda
+    rng = np.random.default_rng(n + M + k + metric)
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+    luts = rng.integers(0, hi, (nq, M, 16)).astype(np.uint8)
+    if hi == 256:
+        luts[0] = np.maximum(luts[0], 200)  # large sums: up to 255 M
+    blocked = bolt.pack_codes(dev(torch, codes))
+    s, i = bolt.topk_u32(blocked, n, M, dev(torch, luts), k, metric)
+    rs, ri = oracle.topk_u32(oracle.scan_u32(codes, luts), k, metric)
+    np.testing.assert_array_equal(i.cpu().numpy(), ri)
+    np.testing.assert_array_equal(s.cpu().numpy().view(np.uint32), rs)
+
+
+def test_topk_u32_explicit_workspace_twice(torch_cuda):
+    """A caller-provided workspace reused by two calls in a row (the
+    histograms and counters are cleared by each call)."""
+    torch = torch_cuda
+    rng = np.random.default_rng(5)
+    n, M, k = 100_003, 512, 50
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+    blocked = bolt.pack_codes(dev(torch, codes))
+    ws = torch.empty(bolt.topk_u32_workspace_bytes(n, M, 2, k), dtype=torch.uint8, device="cuda")
+    for metric in (bolt.METRIC_L2, bolt.METRIC_DOT):
+        luts = rng.integers(0, 256, (2, M, 16)).astype(np.uint8)
+        s, i = bolt.topk_u32(blocked, n, M, dev(torch, luts), k, metric, workspace=ws)
+        rs, ri = oracle.topk_u32(oracle.scan_u32(codes, luts), k, metric)
+        np.testing.assert_array_equal(i.cpu().numpy(), ri)
+        np.testing.assert_array_equal(s.cpu().numpy().view(np.uint32), rs)
 
 
 def test_more_than_256_codebooks_end_to_end(torch_cuda):
