@@ -170,6 +170,24 @@ int bolt_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts,
               int64_t *out_idx, void *workspace, int64_t workspace_bytes,
               void *stream);
 
+/* Fused scan + exact top-k for 1 <= M <= 4096 codebooks over uint32 sums
+ * (Sec. 3.1: the approximate distance sums all M tables; bolt_topk's uint16
+ * sums hold it only up to M = 256).  Same order as bolt_topk -- L2 and L1
+ * ascending, dot descending, ties to the lower vector index, k > n padded
+ * with index -1 and sum 0 -- with the sums of the best k as uint32.
+ * out_sums: nq x k uint32, out_idx: nq x k int64, 1 <= k <= 1024,
+ * n < 2^31, nq <= 65535.  workspace: device scratch of at least
+ * bolt_topk_u32_workspace_bytes(n, M, nq, k) bytes (it holds every sum,
+ * 4 n nq bytes, plus histograms and k candidates per query), 256-byte
+ * aligned, or NULL to allocate and free it stream-ordered inside the call.
+ * Calls sharing one workspace must not overlap on the GPU.  The kernels
+ * have no device waits. */
+int64_t bolt_topk_u32_workspace_bytes(int64_t n, int32_t M, int64_t nq, int32_t k);
+int bolt_topk_u32(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts,
+                  int64_t nq, int32_t k, int32_t metric, uint32_t *out_sums,
+                  int64_t *out_idx, void *workspace, int64_t workspace_bytes,
+                  void *stream);
+
 /* Allocation-free variant of bolt_topk (the paper has no counterpart: this is
  * an interface for callers that may not allocate device memory during the
  * call -- e.g. code issuing work while a CUDA graph is being captured under a

@@ -33,6 +33,9 @@ _lib = None
 _SIGS = {
     "bolt_last_error": ([], C.c_char_p),
     "bolt_probe_int_lanes": ([C.POINTER(C.c_double)], C.c_int),
+    "bolt_topk_u32_workspace_bytes": ([C.c_int64, C.c_int32, C.c_int64, C.c_int32], C.c_int64),
+    "bolt_topk_u32": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
+                       C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "bolt_probe_lookup_core": ([C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.POINTER(C.c_float), C.c_void_p],
                                C.c_int),
     "bolt_version": ([], C.c_char_p),
@@ -307,6 +310,31 @@ def topk(codes, n, M, luts, k, metric, out_sums=None, out_idx=None, workspace=No
                            _ptr(workspace), wbytes, _stream(stream)))
     if check:
         check_topk(out_idx)
+    return out_sums, out_idx
+
+
+def topk_u32_workspace_bytes(n, M, nq, k):
+    v = int(lib().bolt_topk_u32_workspace_bytes(n, M, nq, k))
+    if v < 0:
+        raise BoltError(EINVAL, lib().bolt_last_error().decode())
+    return v
+
+
+def topk_u32(codes, n, M, luts, k, metric, out_sums=None, out_idx=None, workspace=None, stream=None):
+    """Top-k for up to 4096 codebooks: (sums (nq, k) int32 tensor holding the
+    uint32 sums (all below 2^20), idx int64 (nq, k)), best first."""
+    torch = _torch()
+    _dev(codes, torch.uint8, "codes")
+    _dev(luts, torch.uint8, "luts")
+    nq = luts.shape[0]
+    dev = luts.device
+    if out_sums is None:
+        out_sums = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    if out_idx is None:
+        out_idx = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    wbytes = workspace.numel() if workspace is not None else 0
+    _check(lib().bolt_topk_u32(_ptr(codes), n, M, _ptr(luts), nq, k, metric, _ptr(out_sums), _ptr(out_idx),
+                               _ptr(workspace), wbytes, _stream(stream)))
     return out_sums, out_idx
 
 

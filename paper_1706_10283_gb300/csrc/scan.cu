@@ -141,6 +141,16 @@ __global__ void __launch_bounds__(kFloatThreads) scan_float_kernel(const uint32_
     }
 }
 
+int launch_scan_u32(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, uint32_t *sums,
+                    cudaStream_t stream) {
+    const int64_t items = num_blocks(n) * nq;
+    int64_t grid = (items + 7) / 8;
+    const int64_t cap = (int64_t)device_sm_count() * 8;
+    if (cap > 0 && grid > cap) grid = cap;
+    scan_u32_kernel<<<(int)grid, 256, 0, stream>>>(reinterpret_cast<const uint32_t *>(codes), n, M, luts, nq, sums);
+    return check_launch("scan_u32_kernel");
+}
+
 static int check_scan_args(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq,
                            const void *out) {
     int rc = check_nm(n, M);
@@ -182,13 +192,7 @@ int bolt_scan_u32(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *lut
     BOLT_REQUIRE(codes && luts && sums, BOLT_EINVAL, "null pointer");
     BOLT_REQUIRE(bolt::aligned(codes, 16) && bolt::aligned(luts, 16), BOLT_EINVAL,
                  "codes and luts must be 16-byte aligned");
-    const int64_t items = bolt::num_blocks(n) * nq;
-    int64_t grid = (items + 7) / 8;
-    const int64_t cap = (int64_t)bolt::device_sm_count() * 8;
-    if (cap > 0 && grid > cap) grid = cap;
-    bolt::scan_u32_kernel<<<(int)grid, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const uint32_t *>(codes),
-                                                                         n, M, luts, nq, sums);
-    return bolt::check_launch("scan_u32_kernel");
+    return bolt::launch_scan_u32(codes, n, M, luts, nq, sums, (cudaStream_t)stream);
 }
 
 int bolt_scan_float(const uint8_t *codes, int64_t n, int32_t M, const float *luts_f32, int64_t nq, float *out,
