@@ -368,6 +368,20 @@ int bolt_fit_quantizer(const float *Qtrain, int64_t nqt, int32_t J, int32_t M,
                        const float *centroids, int32_t metric, float *a_host,
                        float *b_host, int32_t *alpha_idx_host, void *stream);
 
+/* ---------------------------------------------------------------- timeout-path tests
+ * Sets the time limit, in nanoseconds, of the waits of the streaming top-k
+ * kernel and of the tensor-core encoder for their own data (bulk copies of
+ * codes, the encoder's ring of copies, conversions and MMAs); ns = 0
+ * restores the default of 1 s.  With a limit of a few nanoseconds those waits
+ * give up at once (limits below 1 us are enforced by non-blocking polls, as
+ * a blocking wait may itself outlast them) and the calls take their failure
+ * path -- top-k rows of
+ * index -2, the encoder's n_rechecked = -1 -- while the waits that drain
+ * copies and MMAs in flight before a CTA exits keep their own 0.1 s bound.
+ * For tests of that path; process-wide, not thread-safe with concurrent
+ * calls.  (The paper has no counterpart.) */
+int bolt_set_wait_limit_ns(uint64_t ns);
+
 /* ---------------------------------------------------------------- measurement probes
  * Roofline denominators for the scan, measured on the device that is
  * current (the paper has no counterpart; these compute no Bolt result).

@@ -33,6 +33,7 @@ _lib = None
 _SIGS = {
     "bolt_last_error": ([], C.c_char_p),
     "bolt_probe_int_lanes": ([C.POINTER(C.c_double)], C.c_int),
+    "bolt_set_wait_limit_ns": ([C.c_uint64], C.c_int),
     "bolt_topk_u32_workspace_bytes": ([C.c_int64, C.c_int32, C.c_int64, C.c_int32], C.c_int64),
     "bolt_topk_u32": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
                        C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),

@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <utility>
 
@@ -30,6 +31,10 @@ int check_launch(const char *what) {
     }
     return BOLT_OK;
 }
+
+static std::atomic<uint64_t> g_data_wait_ns{1000000000ull};
+
+uint64_t data_wait_limit_ns() { return g_data_wait_ns.load(std::memory_order_relaxed); }
 
 int device_sm_count() {
     static std::mutex mu;
@@ -110,6 +115,12 @@ extern "C" {
 const char *bolt_last_error(void) { return bolt::g_err; }
 
 const char *bolt_version(void) { return "bolt-gb300 0.1 (sm_103a)"; }
+
+int bolt_set_wait_limit_ns(uint64_t ns) {
+    bolt::clear_error();
+    bolt::g_data_wait_ns.store(ns == 0 ? 1000000000ull : ns, std::memory_order_relaxed);
+    return BOLT_OK;
+}
 
 int64_t bolt_codes_bytes(int64_t n, int32_t M) {
     if (n < 0 || M < 1 || M > bolt::kMaxWideM) return -1;

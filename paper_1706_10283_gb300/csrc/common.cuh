@@ -43,6 +43,11 @@ __host__ __device__ inline int64_t num_blocks(int64_t n) { return (n + kBlockVec
 
 int device_sm_count();  // SMs of the current device (cached per device)
 
+// Time limit of the kernels' waits for their own data (bulk copies, MMAs):
+// 1 s unless bolt_set_wait_limit_ns changed it (tests of the timeout path).
+// Waits that drain copies in flight after a failure keep their own limits.
+uint64_t data_wait_limit_ns();
+
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (device, kernel)
 // and size: later launches (including ones under stream capture) make no
 // attribute call.
@@ -95,6 +100,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Non-blocking test of a phase (mbarrier.try_wait may itself suspend the
+// thread until the phase completes).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -107,6 +126,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     while (!mbar_try_wait(bar, parity))
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
+// Limits below kPollBelowNs (tests of the timeout path) are enforced by
+// polling with the non-blocking test, so that the limit and not the
+// hardware's suspend time decides when the wait gives up.
+constexpr uint64_t kPollBelowNs = 1000;
+
+__device__ __forceinline__ bool mbar_poll_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_test_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_test_wait(bar, parity))
         if (globaltimer_ns() - t0 > limit_ns) return false;
     return true;
 }

@@ -43,7 +43,9 @@ namespace bolt {
 constexpr int kTcRows = 128;      // vectors per tile: MMA M and TMEM lanes
 constexpr int kTcKC = 32;         // dims per chunk: two K = 16 slices
 constexpr int kTcStageBytes = kTcRows * kTcKC * 4;  // one 128 x 32 fp32 chunk (TMA box), 16 KB
-constexpr uint64_t kTcWait = 1000000000ull;  // 1 s bound on every wait
+// 1 s; divided by 10, the bound on draining copies and MMAs in flight after a
+// failure (the roles' waits for one another use data_wait_limit_ns())
+constexpr uint64_t kTcWait = 1000000000ull;
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
@@ -191,14 +193,19 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t pari
     return ok != 0;
 }
 
-// Wait for phase `par` of bar; false if it does not complete within kTcWait
+// Wait for phase `par` of bar; false if it does not complete within limit_ns
 // (the failure flag is then set) or another role has already failed.
-__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t par, volatile uint32_t *fail) {
+__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t par, volatile uint32_t *fail, uint64_t limit_ns) {
+    if (limit_ns < kPollBelowNs) {  // tests of the timeout path: non-blocking polls decide
+        const bool ok = mbar_poll_bounded(bar, par, limit_ns);
+        if (!ok) *fail = 1u;
+        return ok && !*fail;
+    }
     if (mbar_try_wait(bar, par)) return true;
     const uint64_t t0 = globaltimer_ns();
     while (!mbar_try_wait_sleep(bar, par)) {
         if (*fail) return false;
-        if (globaltimer_ns() - t0 > kTcWait) {
+        if (globaltimer_ns() - t0 > limit_ns) {
             *fail = 1u;
             return false;
         }
@@ -221,7 +228,7 @@ template <int S>
 __global__ void __launch_bounds__(kWsThreads, 1)
     encode_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float *__restrict__ Xg, int64_t n, int32_t J,
                      int32_t M, const float *__restrict__ C, uint32_t *__restrict__ codes,
-                     unsigned long long *__restrict__ n_rechecked, int kWsX) {
+                     unsigned long long *__restrict__ n_rechecked, int kWsX, uint64_t wait_ns) {
     using SH = TcShape<S>;
     using WS = WsShape<S>;
     constexpr int NB = WS::NB;
@@ -338,7 +345,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             uint32_t q = 0;
             for (; q < total; ++q) {
                 const uint32_t xs = q % kWsX;
-                if (q >= kWsX && !ws_wait(&bars[kBarXFree + xs], ((q / kWsX) - 1) & 1u, fail)) break;
+                if (q >= kWsX && !ws_wait(&bars[kBarXFree + xs], ((q / kWsX) - 1) & 1u, fail, wait_ns)) break;
                 mbar_arrive_expect_tx(&bars[kBarXFull + xs], (uint32_t)kTcStageBytes);
                 tma_load_2d(X32 + (size_t)xs * kTcStageBytes, &xmap, (int)(q % nchunks) * kTcKC,
                             (int)(q_tile(q) * kTcRows), &bars[kBarXFull + xs]);
@@ -356,8 +363,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             uint32_t q = 0;
             for (; q < total; ++q) {
                 const uint32_t a = q % kWsA, bb = q % NB;
-                if (!ws_wait(&bars[kBarAFull + a], (q / kWsA) & 1u, fail)) break;
-                if (q >= (uint32_t)NB && !ws_wait(&bars[kBarAccFree + bb], ((q / NB) - 1) & 1u, fail)) break;
+                if (!ws_wait(&bars[kBarAFull + a], (q / kWsA) & 1u, fail, wait_ns)) break;
+                if (q >= (uint32_t)NB && !ws_wait(&bars[kBarAccFree + bb], ((q / NB) - 1) & 1u, fail, wait_ns)) break;
                 tc_fence_after();
                 const int c = (int)(q % nchunks);
                 const uint32_t a_base = a_addr + a * kABytes;
@@ -386,9 +393,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         const int r = (warp - kConvWarp0) * 32 + lane;
         for (uint32_t q = 0; q < total; ++q) {
             const uint32_t xs = q % kWsX, a = q % kWsA, bb = q % NB;
-            bool ok = ws_wait(&bars[kBarXFull + xs], (q / kWsX) & 1u, fail);
-            if (ok && q >= kWsA) ok = ws_wait(&bars[kBarAFree + a], ((q / kWsA) - 1) & 1u, fail);
-            if (ok && q >= (uint32_t)NB) ok = ws_wait(&bars[kBarNFree + bb], ((q / NB) - 1) & 1u, fail);
+            bool ok = ws_wait(&bars[kBarXFull + xs], (q / kWsX) & 1u, fail, wait_ns);
+            if (ok && q >= kWsA) ok = ws_wait(&bars[kBarAFree + a], ((q / kWsA) - 1) & 1u, fail, wait_ns);
+            if (ok && q >= (uint32_t)NB) ok = ws_wait(&bars[kBarNFree + bb], ((q / NB) - 1) & 1u, fail, wait_ns);
             if (!__all_sync(0xFFFFFFFFu, ok)) break;
             const uint8_t *xs_stage = X32 + (size_t)xs * kTcStageBytes;
             uint8_t *Ab = A + (size_t)a * kABytes;
@@ -437,8 +444,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             bool ok = true;
             for (uint32_t j = 0; j < nq; ++j) {
                 const uint32_t q = q0 + j, bb = q % NB;
-                if (ok) ok = ws_wait(&bars[kBarAccFull + bb], (q / NB) & 1u, fail);
-                if (ok) ok = ws_wait(&bars[kBarNFull + bb], (q / NB) & 1u, fail);
+                if (ok) ok = ws_wait(&bars[kBarAccFull + bb], (q / NB) & 1u, fail, wait_ns);
+                if (ok) ok = ws_wait(&bars[kBarNFull + bb], (q / NB) & 1u, fail, wait_ns);
             }
             if (!__all_sync(0xFFFFFFFFu, ok)) break;
             tc_fence_after();
@@ -599,7 +606,8 @@ static int launch_tc(const float *X, int64_t n, int32_t J, int32_t M, const floa
     rc = make_x_map(X, n, J, &map);
     if (rc) return rc;
     kern<<<(int)grid, kWsThreads, smem, stream>>>(map, X, n, J, M, C, reinterpret_cast<uint32_t *>(codes),
-                                                  reinterpret_cast<unsigned long long *>(n_rechecked), nx);
+                                                  reinterpret_cast<unsigned long long *>(n_rechecked), nx,
+                                                  data_wait_limit_ns());
     return check_launch("encode_tc_kernel");
 }
 

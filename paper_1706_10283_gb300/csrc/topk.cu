@@ -49,7 +49,10 @@
 
 namespace bolt {
 
-constexpr uint64_t kWaitLimit = 1000000000ull;  // 1 s bound on any mbarrier wait
+// 1 s: the bound on the warps' wait for one another and, divided by 10, on
+// draining copies in flight after a failure (waits for the CTA's own code
+// copies use data_wait_limit_ns(), 1 s by default)
+constexpr uint64_t kWaitLimit = 1000000000ull;
 constexpr int kMaxStages = 8;
 constexpr size_t kStageBudget = 128 * 1024;
 constexpr int kMaxK = 1024;
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     topk_kernel(const uint32_t *__restrict__ codes, int64_t n, int32_t M, const uint8_t *__restrict__ luts,
                 int32_t k, int32_t metric, TopkWS ws, int stages, int cap, int hshift, int64_t blocks_per_cta,
                 int out_cap, uint16_t *__restrict__ out_sums, int64_t *__restrict__ out_idx,
-                const uint32_t *__restrict__ active) {
+                const uint32_t *__restrict__ active, uint64_t wait_ns) {
     constexpr int T = WARPS * 32;
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -388,7 +391,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     uint32_t *chist = reinterpret_cast<uint32_t *>(p);  // [kSeedBins] coarse counts of the first round
     // misc: [0] buffer count [1] insert threshold [2] failure flag [3] last CTA
     //       [26], [27] tie rule: a key with s' == misc[26] and index > misc[27] is not inserted
-    //       [4] scratch [8..26) BinSel results [32..48) keep_if counts [64..66) BlockSel
+    //       [4] scratch [8..26) BinSel results [32..48) keep_if counts [48..50) test barrier
+    //       [64..66) BlockSel
     BinSel<T> bins{hist, misc + 8, hshift};
     BlockSel<T> sel{hist, misc + 64};
     uint32_t *wcnt = misc + 32;
@@ -430,7 +434,17 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
 
     const uint4 *lut_g = reinterpret_cast<const uint4 *>(luts + q * M * kK);
     for (int i = tid; i < M; i += T) lut[i] = lut_g[i];
+    // Tests of the timeout path (data-wait limit below kPollBelowNs): every
+    // warp's first wait is on misc[48..49], an mbarrier that nothing arrives
+    // on, so it gives up and the CTA takes its failure path with real copies
+    // in flight (they complete on their own barriers and are drained).
+    const bool test_stall = wait_ns < kPollBelowNs;
+    uint64_t *dead = reinterpret_cast<uint64_t *>(misc + 48);
     if (tid == 0) {
+        if (test_stall) {
+            mbar_init(dead, 1);
+            fence_mbar_init();
+        }
         misc[0] = 0;
         misc[1] = kThrAll;
         misc[2] = 0;
@@ -585,8 +599,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     for (uint32_t u = u_lo + warp;; u += WARPS, ++j) {
         if (requests()) cooperative();
         if (u >= u_hi || failed) break;
-        if (!__all_sync(0xFFFFFFFFu, mbar_try_wait(&mybars[st], par))) {
-            const bool ok = mbar_wait_bounded(&mybars[st], par, kWaitLimit);
+        uint64_t *wbar = test_stall && j == 0 ? dead : &mybars[st];
+        if (!__all_sync(0xFFFFFFFFu, test_stall ? mbar_test_wait(wbar, par) : mbar_try_wait(wbar, par))) {
+            const bool ok = test_stall ? mbar_poll_bounded(wbar, par, wait_ns) : mbar_wait_bounded(wbar, par, wait_ns);
             if (!__all_sync(0xFFFFFFFFu, ok)) {
                 failed = true;
                 if (j == 0) seed_barrier(seeders);  // the other seeders still count on this warp
@@ -1016,7 +1031,7 @@ static int launch_w(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *l
     kern<<<grid, WARPS * 32, plan.smem_bytes, stream>>>(reinterpret_cast<const uint32_t *>(codes), n, M, luts, k,
                                                          metric, w, plan.stages, plan.cap, plan.hshift,
                                                          plan.blocks_per_cta, plan.out_cap, out_sums, out_idx,
-                                                         active);
+                                                         active, data_wait_limit_ns());
     return check_launch("topk_kernel");
 }
 
