@@ -210,20 +210,21 @@ def test_topk_bitexact(torch_cuda, metric, n, M, k):
 @pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
 @pytest.mark.parametrize("hi,nq", [(2, 4), (16, 5), (256, 37), (16, 1), (2, 1)])
 def test_topk_large_database_paths(torch_cuda, metric, hi, nq):
-    """3,000,000 vectors (beyond the shared-memory size class).  With 4 or
+    """4,000,000 vectors (103 blocks per CTA: beyond the shared-memory size
+    class, which holds up to ~3.3M vectors at M = 16, k = 100).  With 4 or
     more queries: sample bound, multi-query filter and select, tables drawn
     from [0, hi): hi = 2 makes every sum tie (candidate overflow: the exact
     streaming fallback runs), hi = 16 makes hundreds of ties at the k-th sum
     (ordered by index), hi = 256 is the ordinary case; 37 queries span tiles
     of 16, 16, 4 and 1.  One query: the fused streaming kernel."""
     rng = np.random.default_rng(hi * 10 + nq + metric)
-    n, M, k = 3_000_000, 16, 100
+    n, M, k = 4_000_000, 16, 100
     codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
     luts = rng.integers(0, hi, (nq, M, 16)).astype(np.uint8)
     check_topk(torch_cuda, codes, luts, k, metric)
 
 
-@pytest.mark.parametrize("n,M,k,nq", [(1000, 8, 10, 1), (100_003, 16, 100, 2), (3_000_000, 16, 50, 5)])
+@pytest.mark.parametrize("n,M,k,nq", [(1000, 8, 10, 1), (100_003, 16, 100, 2), (4_000_000, 16, 50, 5)])
 def test_topk_l1_tables_rank_ascending(torch_cuda, n, M, k, nq):
     """L1 tables (the L_p family with p = 1): top-k ranks by ascending sum,
     through every size class (shared-memory, streaming, multi-query)."""
@@ -259,7 +260,7 @@ def test_topk_sorted_input_worst_case(torch_cuda):
 @pytest.mark.parametrize("pattern", ["concentrated", "sorted"])
 @pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
 def test_topk_streaming_kernel_stress(torch_cuda, pattern, metric):
-    """The streaming kernel (one query, 3,000,000 vectors) where one CTA's
+    """The streaming kernel (one query, 4,000,000 vectors) where one CTA's
     range decides the top k: "concentrated" puts 20,000 vectors with small,
     sparsely tied sums inside one range (its local thresholds meet the
     global k-th sum, where warps out of lockstep matter); "sorted" makes the
@@ -267,7 +268,7 @@ def test_topk_streaming_kernel_stress(torch_cuda, pattern, metric):
     Twelve repeated launches must all equal the oracle."""
     torch = torch_cuda
     rng = np.random.default_rng(71 + metric)
-    n, M, k = 3_000_000, 16, 100
+    n, M, k = 4_000_000, 16, 100
     luts = rng.integers(0, 256, (1, M, 16)).astype(np.uint8)
     if pattern == "concentrated":
         codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
