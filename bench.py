@@ -818,9 +818,10 @@ def approx_matmul_standalone(hbm_peak):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one topk_kernel launch
-# (ncu, one query, 8,000,000 vectors, cold caches) scaled by 50M / 8M, or
-# None until a capture of the current kernel exists
-TOPK_TRAFFIC_50M = None
+# (ncu, one query, 8,000,000 vectors, cold caches: 64,114,176 + 25,856
+# bytes, profiles/topk_kernel_mixture_8m.md) scaled by 50M / 8M; the traffic
+# is the codes once, proportional to n.  None once the kernel changes.
+TOPK_TRAFFIC_50M = (64_114_176 + 25_856) * 50 // 8
 
 
 def roofline_topk_50m(launch_ms, n, M, hbm_peak, peak_kind, core_us):
