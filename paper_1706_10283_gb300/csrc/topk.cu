@@ -36,12 +36,16 @@
 // Every 4 rounds one warp in turn reads the coarse then the fine counts and
 // lowers the CTA's threshold to that bin, without stopping the other warps.
 //
-// Merge.  Each CTA appends its candidates up to the current global bound
-// (at most 2k, else its exact top k) to a per-query list; the last CTA to
-// finish (atomic ticket) gathers the lists into shared memory (when they
-// hold more than 1024 keys, only the keys at or below the final bound bin of
-// the global histogram), selects the exact k smallest keys, sorts them and
-// writes the result.
+// Merge.  Each CTA writes its candidates up to the current global bound (at
+// most 2k, else its exact top k) to its own slot of a per-query list (the
+// count, then the keys); the last CTA to finish (atomic ticket) reads the
+// slot counts while one warp finds the final bound bin of the global
+// histogram, gathers the keys into shared memory (when there are more than
+// 1024, only those at or below that bin), selects the exact k smallest keys,
+// sorts them and writes the result.
+//
+// Tables.  For dot the CTA complements its tables (255 - D is the byte
+// complement), so the lookups produce s' directly.
 #include <mutex>
 
 #include "scan_core.cuh"
@@ -432,8 +436,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         }
     }
 
+    // For dot the tables are complemented (255 - D is the byte complement),
+    // so the scan yields s' = 255*M - S directly.
     const uint4 *lut_g = reinterpret_cast<const uint4 *>(luts + q * M * kK);
-    for (int i = tid; i < M; i += T) lut[i] = lut_g[i];
+    const uint32_t lut_x = metric == BOLT_METRIC_DOT ? 0xFFFFFFFFu : 0u;
+    for (int i = tid; i < M; i += T) {
+        const uint4 t = lut_g[i];
+        lut[i] = make_uint4(t.x ^ lut_x, t.y ^ lut_x, t.z ^ lut_x, t.w ^ lut_x);
+    }
     // Tests of the timeout path (data-wait limit below kPollBelowNs): every
     // warp's first wait is on misc[48..49], an mbarrier that nothing arrives
     // on, so it gives up and the CTA takes its failure path with real copies
@@ -508,13 +518,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
 
     bool failed = false;
     const uint32_t smax = 255u * (uint32_t)M;  // largest possible sum
-    const uint32_t smax2 = smax | (smax << 16);
     const bool swar = smax <= 0x7FFFu;  // sums fit in 15 bits (M <= 128)
     const uint32_t gate = (uint32_t)(cap - WARPS * BPI * kBlockVecs / 2);  // compact above this count
     // before the first compaction: compact as soon as a few blocks are in
     const uint32_t early = min(gate, max((uint32_t)(2 * k), (uint32_t)(WARPS * BPI * kBlockVecs)));
     const uint32_t one = kMulOne;
-    const uint32_t neg1 = 0u - kMulOne;
     bool compacted = false;  // same value in every thread (set in cooperative())
 
     // Cooperative compaction.  Warps run independently; a warp that finds the
@@ -595,6 +603,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     const uint32_t seeders = u_hi > u_lo ? min((uint32_t)WARPS, u_hi - u_lo) : 0u;
     uint32_t st = 0, par = 0;  // stage and parity of this warp's current unit
     uint32_t j = 0;            // units done by this warp
+    uint32_t next_refresh = 4u * (uint32_t)warp + 1u;  // this warp's next refresh round
 
     for (uint32_t u = u_lo + warp;; u += WARPS, ++j) {
         if (requests()) cooperative();
@@ -647,32 +656,19 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             par ^= 1u;
         }
         // sw[h]: the unit's 8 sums s' per lane in 16-bit lanes (s'_0 | s'_2 << 16,
-        // s'_1 | s'_3 << 16, then vectors 4..7); sum_of(h, i) is vector i's s'
+        // s'_1 | s'_3 << 16, then vectors 4..7); sum_of(h, i) is vector i's s'.
+        // Vector vbase + 256 h + i exists iff its index is below n (a missing
+        // second block of the last unit lies past n).
         uint32_t sw[BPI][4];
-        uint32_t v0[BPI];
-        bool tail[BPI], valid[BPI];
 #pragma unroll
-        for (int h = 0; h < BPI; ++h) {
-            const uint32_t b = u * BPI + h;
-            valid[h] = b <= last_block;
-            tail[h] = b == last_block;
-            v0[h] = b * kBlockVecs + 8u * lane;
-            uint32_t e_lo, o_lo, e_hi, o_hi;
-            acc[h].finish(e_lo, o_lo, e_hi, o_hi);
-            if (metric == BOLT_METRIC_DOT) {  // s' = 255*M - S in each 16-bit lane (no borrow)
-                e_lo = imad(e_lo, neg1, smax2);
-                o_lo = imad(o_lo, neg1, smax2);
-                e_hi = imad(e_hi, neg1, smax2);
-                o_hi = imad(o_hi, neg1, smax2);
-            }
-            sw[h][0] = e_lo;
-            sw[h][1] = o_lo;
-            sw[h][2] = e_hi;
-            sw[h][3] = o_hi;
-        }
+        for (int h = 0; h < BPI; ++h) acc[h].finish(sw[h][0], sw[h][1], sw[h][2], sw[h][3]);
+        const uint32_t vbase = u * (uint32_t)(BPI * kBlockVecs) + 8u * lane;
+        // every block of the unit lies before the last block: all its vectors exist
+        const bool whole = u * (uint32_t)BPI + (uint32_t)(BPI - 1) < last_block;
         auto sum_of = [&](int h, int i) -> uint32_t {
             return (sw[h][(i & 1) + 2 * (i >> 2)] >> (16 * ((i >> 1) & 1))) & 0xFFFFu;
         };
+        auto exists = [&](int h, int i) -> bool { return vbase + (uint32_t)(h * kBlockVecs + i) < (uint32_t)n; };
         uint32_t thr = vmisc[1];
         if (j == 0) {
             // Seed the threshold from the CTA's first round: every warp counts
@@ -685,7 +681,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const uint32_t sp = sum_of(h, i);
-                    if (valid[h] && (!tail[h] || v0[h] + i < (uint32_t)n)) {
+                    if (whole || exists(h, i)) {
                         atomicAdd(&hist[sp >> hshift], 1u);
                         atomicAdd(&chist[sp >> (hshift + 4)], 1u);
                     }
@@ -717,21 +713,19 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
                 }
             }
         }
-        bool maybe = false;
+        // Threshold filter: with s' < 2^15 the top bit of (s' + 2^15 - thr) in
+        // each 16-bit lane is clear exactly when s' < thr, with no borrow
+        // between lanes; one AND over the unit's words tests all its sums.
+        // The last unit (and any M with wider sums) goes to the exact test.
+        bool maybe = true;
+        if (whole && swar && thr <= 0x7FFFu) {
+            const uint32_t nt2 = 0x80008000u - (thr | (thr << 16));
+            uint32_t d = 0xFFFFFFFFu;
 #pragma unroll
-        for (int h = 0; h < BPI; ++h) {
-            bool mh = valid[h];
-            if (swar && thr <= 0x7FFFu) {
-                // s' < 2^15: the top bit of (s' + 2^15 - thr) in each lane is
-                // clear exactly when s' < thr, with no borrow between lanes
-                // (s' | 2^15 = s' + 2^15 since bit 15 of s' is clear).
-                const uint32_t nt2 = 0x80008000u - (thr | (thr << 16));
-                const uint32_t d = imad(sw[h][0], one, nt2) & imad(sw[h][1], one, nt2) & imad(sw[h][2], one, nt2) &
-                                   imad(sw[h][3], one, nt2);
-                mh = mh && (~d & 0x80008000u) != 0u;
-            }
-            if (tail[h]) mh = mh && v0[h] < (uint32_t)n;
-            maybe = maybe || mh;
+            for (int h = 0; h < BPI; ++h)
+                d &= imad(sw[h][0], one, nt2) & imad(sw[h][1], one, nt2) & imad(sw[h][2], one, nt2) &
+                     imad(sw[h][3], one, nt2);
+            maybe = (~d & 0x80008000u) != 0u;
         }
         if (__any_sync(0xFFFFFFFFu, maybe)) {
             // first-round keys are already in the global counts (seeding)
@@ -746,9 +740,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const uint32_t sp = sum_of(h, i);
-                        if (valid[h] && sp < thr && (!tail[h] || v0[h] + i < (uint32_t)n) &&
-                            !(sp == tie_v && v0[h] + i > tie_i))
-                            cm |= 1u << (8 * h + i);
+                        const uint32_t v = vbase + (uint32_t)(h * kBlockVecs + i);
+                        if (sp < thr && v < (uint32_t)n && !(sp == tie_v && v > tie_i)) cm |= 1u << (8 * h + i);
                     }
                 const uint32_t c = __popc(cm);
                 uint32_t incl = c;
@@ -780,7 +773,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
                         for (int i = 0; i < 8; ++i) {
                             if (cm & (1u << (8 * h + i))) {
                                 const uint32_t sp = sum_of(h, i);
-                                keys[pos++] = ((uint64_t)sp << 32) | (uint64_t)(v0[h] + i) | counted;
+                                keys[pos++] =
+                                    ((uint64_t)sp << 32) | (uint64_t)(vbase + (uint32_t)(h * kBlockVecs + i)) | counted;
                             }
                         }
                     break;
@@ -796,11 +790,17 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             if (lane == 0 && vmisc[0] > (compacted ? gate : early)) atomicOr(&misc[6], 1u);
         }
         // every 4 rounds one warp (in turn) lowers the threshold to the
-        // global bound
-        if ((j & 3u) == 1u && (uint32_t)warp == (j >> 2) % WARPS) warp_refresh();
+        // global bound: warp w at its rounds 4w + 1 + 4 WARPS t
+        if (j == next_refresh) {
+            warp_refresh();
+            next_refresh += 4u * WARPS;
+        }
     }
-    // This warp is out of blocks: keep joining cooperative phases until every
-    // warp is done (each of them reaches this point in bounded time).
+    // This warp is out of blocks: start the loads of the global histogram
+    // for the final bound (a later cooperative phase reloads them), then keep
+    // joining cooperative phases until every warp is done (each of them
+    // reaches this point in bounded time).
+    prefetch();
     if (lane == 0) atomicAdd(&misc[7], 1u);
     {
         const uint64_t t0 = globaltimer_ns();
@@ -835,9 +835,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     if (failed) atomicOr(&misc[2], 1u);
     __syncthreads();
 
-    // Candidates of this CTA up to the global bound (at most 2k of them).
+    // Candidates of this CTA up to the global bound (at most 2k of them),
+    // published to the CTA's own slot of the query's list: slot[0] holds the
+    // count, the keys follow.
     int cnt = (int)vmisc[0];
-    prefetch();
     const uint32_t bg = finish(cnt);
     cnt = keep_if<T>(keys, cnt, wcnt,
                      [&](uint64_t key) { return ((uint32_t)(kv(key) >> 32) >> hshift) <= bg; });
@@ -845,12 +846,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         const uint64_t kth = sel.kth_key(keys, cnt, (uint32_t)k);
         cnt = keep_if<T>(keys, cnt, wcnt, [&](uint64_t key) { return kv(key) <= kth; });
     }
-    if (tid == 0) misc[4] = atomicAdd(&ws.fill[q], (uint32_t)cnt);
-    __syncthreads();
-    uint64_t *list = ws.cand + q * (int64_t)(out_cap * G);
-    const uint32_t base = vmisc[4];
-    for (int i = tid; i < cnt; i += T) list[base + i] = kv(keys[i]);
-    if (tid == 0 && misc[2]) atomicOr(&ws.status[q], 1u);
+    const int64_t slot_len = (int64_t)out_cap + 1;
+    uint64_t *slots = ws.cand + q * (slot_len * G);
+    uint64_t *slot = slots + cta * slot_len;
+    for (int i = tid; i < cnt; i += T) slot[1 + i] = kv(keys[i]);
+    if (tid == 0) {
+        slot[0] = (uint64_t)cnt;
+        if (misc[2]) atomicOr(&ws.status[q], 1u);
+    }
     __threadfence();
     __syncthreads();
     if (tid == 0) misc[3] = (atomicAdd(&ws.ticket[q], 1u) == (uint32_t)(G - 1)) ? 1u : 0u;
@@ -858,30 +861,68 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     if (vmisc[3] == 0) return;
     __threadfence();
 
-    // Last CTA: final bound from the complete histogram (unless the lists
-    // are short enough to rank whole), gather, select, sort.
-    const uint32_t total = __ldcg(&ws.fill[q]);
-    uint32_t bfin = 0xFFFFFFFFu;
-    if (total > (uint32_t)kRankSortMax) {
-        // one warp reads the two-level global counts (complete: every CTA
-        // added its counts before taking its ticket)
-        if (warp == 0) {
-            uint32_t cbin, fbin, in_bin, c[8];
-            const bool ok = warp_kth_bin<true>(gcoarse, ghist, (uint32_t)k, lane, cbin, fbin, in_bin, c);
-            if (lane == 0) misc[5] = ok ? fbin : 0xFFFFFFFFu;
+    // Last CTA.  Warp 0: exclusive prefix of the slot counts (off[c], with
+    // off[G] the total) and the failure status; warp 1, at the same time: the
+    // final bound bin from the complete global histogram (every CTA added
+    // its counts before taking its ticket).  Then all threads gather the
+    // keys, only those at or below the bound bin when there are more than
+    // kRankSortMax of them; the (unique) keys are selected and sorted below.
+    uint32_t *off = hist;  // [G + 1]; the histogram area is free in the last CTA
+    if (warp == 0) {
+        uint32_t run = 0;
+        for (int c0 = 0; c0 < G; c0 += 256) {
+            uint32_t v[8], loc = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int c = c0 + lane * 8 + i;
+                v[i] = c < G ? (uint32_t)__ldcg(slots + c * slot_len) : 0u;
+                loc += v[i];
+            }
+            uint32_t incl = loc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            uint32_t e = run + incl - loc;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int c = c0 + lane * 8 + i;
+                if (c < G) off[c] = e;
+                e += v[i];
+            }
+            run += __shfl_sync(0xFFFFFFFFu, incl, 31);
         }
-        __syncthreads();
-        bfin = vmisc[5];
+        if (lane == 0) {
+            off[G] = run;
+            misc[4] = 0;
+            misc[2] = __ldcg(&ws.status[q]);
+        }
+    } else if (warp == 1) {
+        uint32_t cbin, fbin, in_bin, c[8];
+        const bool ok = warp_kth_bin<true>(gcoarse, ghist, (uint32_t)k, lane, cbin, fbin, in_bin, c);
+        if (lane == 0) misc[5] = ok ? fbin : 0xFFFFFFFFu;
     }
-    uint64_t *mk = reinterpret_cast<uint64_t *>(smem);
-    if (tid == 0) misc[4] = 0;
     __syncthreads();
+    const uint32_t total = vmisc_hist(off, G);
+    const uint32_t bfin = total > (uint32_t)kRankSortMax ? vmisc[5] : 0xFFFFFFFFu;
+    uint64_t *mk = reinterpret_cast<uint64_t *>(smem);
     for (uint32_t e0 = 0; e0 < total; e0 += 4 * T) {
         uint64_t v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const uint32_t e = e0 + u * T + tid;
-            v[u] = e < total ? __ldcg(list + e) : ~0ull;
+            v[u] = ~0ull;
+            if (e < total) {
+                // slot of entry e: the last c with off[c] <= e
+                int lo = 0, hi = G - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (off[mid] <= e) lo = mid;
+                    else hi = mid - 1;
+                }
+                v[u] = __ldcg(slots + lo * slot_len + 1 + (e - off[lo]));
+            }
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -889,7 +930,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     }
     __syncthreads();
     int g = (int)vmisc[4];
-    const bool bad = __ldcg(&ws.status[q]) != 0u;
+    const bool bad = vmisc[2] != 0u;
     auto emit = [&](int r, uint64_t key) {
         const uint32_t sp = (uint32_t)(key >> 32);
         out_sums[q * k + r] = (uint16_t)(metric == BOLT_METRIC_DOT ? 255u * (uint32_t)M - sp : sp);
@@ -981,7 +1022,7 @@ int plan_topk_stream(int64_t n, int32_t M, int32_t k, TopkPlan *plan) {
     plan->cap = cap;
     plan->hshift = hshift;
     plan->out_cap = (int)out_cap;
-    plan->list_cap = (int)(g * out_cap);
+    plan->list_cap = (int)(g * (out_cap + 1));  // one slot per CTA: count, then keys
     plan->blocks_per_cta = nu > 0 ? (nu + g - 1) / g : 0;  // units per CTA
     plan->smem_bytes = region + align_up((size_t)M * 16, 16) + (size_t)warps * kMaxStages * 8 + kBins * 4 + 128 * 4 +
                        kSeedBins * 4;
@@ -989,7 +1030,7 @@ int plan_topk_stream(int64_t n, int32_t M, int32_t k, TopkPlan *plan) {
 }
 
 size_t topk_header_bytes(int64_t nq) {
-    return align_up((size_t)nq * 12, 256) + (size_t)nq * (kBins + kBins / 16) * 4;
+    return align_up((size_t)nq * 8, 256) + (size_t)nq * (kBins + kBins / 16) * 4;
 }
 
 int64_t topk_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k) {
@@ -1006,10 +1047,9 @@ int64_t topk_stream_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k)
 TopkWS carve_topk_ws(void *ws, const TopkPlan &plan, int64_t nq, int32_t k) {
     uint8_t *p = static_cast<uint8_t *>(ws);
     TopkWS w;
-    w.fill = reinterpret_cast<uint32_t *>(p);
-    w.ticket = w.fill + nq;
+    w.ticket = reinterpret_cast<uint32_t *>(p);
     w.status = w.ticket + nq;
-    p += align_up((size_t)nq * 12, 256);
+    p += align_up((size_t)nq * 8, 256);
     w.ghist = reinterpret_cast<uint32_t *>(p);
     p += (size_t)nq * kBins * 4;
     w.gcoarse = reinterpret_cast<uint32_t *>(p);

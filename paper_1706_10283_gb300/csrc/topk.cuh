@@ -28,19 +28,18 @@ struct TopkPlan {
     int cap;              // candidate-buffer entries per CTA
     int hshift;           // (s) histogram bin width 2^hshift
     int out_cap;          // candidates one CTA may append (k <= out_cap <= 2k)
-    int list_cap;         // per-query candidate list capacity (grid * out_cap)
+    int list_cap;         // per-query candidate list length: grid slots of out_cap + 1 entries
     int64_t blocks_per_cta;  // units of work per CTA
     size_t smem_bytes;    // (s)
 };
 
 // Per-query device state in the workspace.
 struct TopkWS {
-    uint32_t *fill;    // [nq] entries appended to the candidate list
     uint32_t *ticket;  // [nq] CTAs finished
     uint32_t *status;  // [nq] bit 0: a bounded wait gave up
     uint32_t *ghist;   // [nq][kBins] counted candidates per sum bin
     uint32_t *gcoarse; // [nq][kBins / 16] the same counts in bins 16 times wider
-    uint64_t *cand;    // [nq][list_cap] candidate keys (sum' << 32 | index)
+    uint64_t *cand;    // [nq][grid][out_cap + 1] per CTA: key count, then keys (sum' << 32 | index)
 };
 
 // Size class by database size and query count: shared-memory kernel
@@ -49,7 +48,7 @@ struct TopkWS {
 int plan_topk(int64_t n, int32_t M, int32_t k, int64_t nq, TopkPlan *plan);
 int64_t topk_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k);
 TopkWS carve_topk_ws(void *ws, const TopkPlan &plan, int64_t nq, int32_t k);
-size_t topk_header_bytes(int64_t nq);  // fill/ticket/status + histograms (zeroed per call)
+size_t topk_header_bytes(int64_t nq);  // ticket/status + histograms (zeroed per call)
 
 bool plan_topk_small(int64_t n, int32_t M, int32_t k, int sms, TopkPlan *plan);
 int64_t topk_small_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k);
