@@ -895,7 +895,6 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         }
         if (lane == 0) {
             off[G] = run;
-            misc[4] = 0;
             misc[2] = __ldcg(&ws.status[q]);
         }
     } else if (warp == 1) {
@@ -907,29 +906,54 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     const uint32_t total = vmisc_hist(off, G);
     const uint32_t bfin = total > (uint32_t)kRankSortMax ? vmisc[5] : 0xFFFFFFFFu;
     uint64_t *mk = reinterpret_cast<uint64_t *>(smem);
+    uint32_t kept_all = 0;
+    int steps = 0;  // binary-search steps over the G slots
+    while ((1 << steps) < G) ++steps;
     for (uint32_t e0 = 0; e0 < total; e0 += 4 * T) {
-        uint64_t v[4];
+        // slot of entry e: the last c with off[c] <= e (four searches in step)
+        uint32_t e[4];
+        int lo[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const uint32_t e = e0 + u * T + tid;
-            v[u] = ~0ull;
-            if (e < total) {
-                // slot of entry e: the last c with off[c] <= e
-                int lo = 0, hi = G - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (off[mid] <= e) lo = mid;
-                    else hi = mid - 1;
-                }
-                v[u] = __ldcg(slots + lo * slot_len + 1 + (e - off[lo]));
+            e[u] = e0 + u * T + tid;
+            lo[u] = 0;
+        }
+        for (int bit = steps - 1; bit >= 0; --bit) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int mid = lo[u] + (1 << bit);
+                if (mid < G && off[mid] <= e[u]) lo[u] = mid;
             }
         }
+        uint64_t v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (v[u] != ~0ull && ((uint32_t)(v[u] >> 32) >> hshift) <= bfin) mk[atomicAdd(&misc[4], 1u)] = v[u];
+            v[u] = e[u] < total ? __ldcg(slots + lo[u] * slot_len + 1 + (e[u] - off[lo[u]])) : ~0ull;
+        // kept keys: warp ballots counted, a prefix over the warps, then the
+        // writes (no shared-memory atomics)
+        uint32_t bal[4], cw = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            bal[u] = __ballot_sync(0xFFFFFFFFu, v[u] != ~0ull && ((uint32_t)(v[u] >> 32) >> hshift) <= bfin);
+            cw += __popc(bal[u]);
+        }
+        if (lane == 0) wcnt[warp] = cw;
+        __syncthreads();
+        uint32_t pos = kept_all, tot = 0;
+        for (int w = 0; w < WARPS; ++w) {
+            const uint32_t c = wcnt[w];
+            pos += w < warp ? c : 0u;
+            tot += c;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (bal[u] & (1u << lane)) mk[pos + __popc(bal[u] & lanemask_lt())] = v[u];
+            pos += __popc(bal[u]);
+        }
+        kept_all += tot;
+        __syncthreads();
     }
-    __syncthreads();
-    int g = (int)vmisc[4];
+    int g = (int)kept_all;
     const bool bad = vmisc[2] != 0u;
     auto emit = [&](int r, uint64_t key) {
         const uint32_t sp = (uint32_t)(key >> 32);

@@ -8,7 +8,8 @@
 // Per CTA (one contiguous range of blocks):
 //   1. one thread starts 1-D bulk copies of the whole code range into shared
 //      memory (chunks of 8 blocks, one mbarrier each) while the others load
-//      the query table;
+//      the query table (complemented for dot: 255 - D is the byte
+//      complement, so the lookups give s' = 255*M - S directly);
 //   2. each warp scans blocks as their chunk lands, writes the 8 sums of each
 //      lane as keys s' (s' = S for L2, 255*M - S for dot; 0xFFFF for padding
 //      vectors) to a shared array in vector order, and counts them in a
@@ -17,19 +18,23 @@
 //      from the histogram (plus a second count inside T's bin when bins are
 //      wider than 1); the CTA adds the per-bin counts of the keys it keeps to
 //      the query's global histogram (one atomic per non-empty bin);
-//   4. an ordered compaction keeps every s' < T and the first k - c_lt
-//      entries with s' == T, in vector order: that is the CTA's exact top-k
-//      with ties to the lower index; it is published to the CTA's slot of a
-//      global list, sorted by (s', index).
-// The last CTA to finish (atomic ticket) reads the global histogram, which
-// gives the k-th smallest s' of the union of the lists and the number of
-// keys below it; every list then contributes a prefix (binary search), the
-// ties at the threshold taken in vector order (CTA ranges are ordered), and
-// the k survivors are sorted and written.
+//   4. every entry with s' <= T is appended (in any order) and ranked: the k
+//      smallest keys (s' << 32 | index) are every s' < T and the lowest
+//      indices with s' == T, the CTA's exact top-k, published to its slot of
+//      a global list sorted by key.  With more than 64 surplus entries equal
+//      to T an ordered compaction keeps the first ones in vector order
+//      instead.
+// The last CTA to finish (atomic ticket) reads the first 16 keys of every
+// list.  If no list longer than 16 has its 16th key at or below the k-th
+// smallest s' of these prefixes, the k smallest prefix keys are the answer.
+// Otherwise it reads the global histogram, which gives the k-th smallest s'
+// of the union of the lists and the number of keys below it; every list then
+// contributes a prefix (binary search), the ties at the threshold taken in
+// vector order (CTA ranges are ordered).  The k survivors are sorted and
+// written.
 #include "topk.cuh"
 
 #include "scan_core.cuh"
-#include "tma.cuh"
 
 namespace bolt {
 
@@ -39,7 +44,7 @@ constexpr int kSmallChunk = 8;  // blocks per bulk copy
 constexpr uint64_t kSmallWait = 1000000000ull;  // 1 s bound on every mbarrier wait
 constexpr int kSmallMiscWords = 64;
 constexpr uint32_t kPad = 0xFFFFu;  // s' of padding vectors (every real s' <= 255 * 256)
-constexpr int kSmallPrefix = 16;     // keys per list the merge copies to shared memory
+constexpr int kSmallPrefix = 16;     // keys per list the merge reads first
 
 // Exclusive block-wide prefix sum of one value per thread (T = 512).
 // wsum: kSmallWarps + 1 words of shared scratch.  Returns the prefix and the
@@ -133,6 +138,76 @@ __device__ __forceinline__ void small_keep(int L, uint32_t T, uint32_t r, F s, E
     __syncthreads();
 }
 
+// Of the n distinct keys of src (shared memory), writes those of rank < nout
+// to dst[rank] (increasing order): each key's rank is the number of smaller
+// keys, counted by P adjacent threads per key.
+__device__ __forceinline__ void small_rank_sort(const uint64_t *src, int n, uint64_t *dst, int nout) {
+    const int tid = threadIdx.x;
+    int P = 1;
+    while (P < 32 && n * P * 2 <= kSmallThreads) P <<= 1;
+    const int part = tid & (P - 1);
+    for (int base = 0; base < n; base += kSmallThreads / P) {
+        const int e = base + tid / P;
+        const uint64_t key = e < n ? src[e] : ~0ull;
+        int r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+        if (e < n) {
+            int j = part;
+            for (; j + 3 * P < n; j += 4 * P) {
+                r0 += src[j] < key ? 1 : 0;
+                r1 += src[j + P] < key ? 1 : 0;
+                r2 += src[j + 2 * P] < key ? 1 : 0;
+                r3 += src[j + 3 * P] < key ? 1 : 0;
+            }
+            for (; j < n; j += P) r0 += src[j] < key ? 1 : 0;
+        }
+        int rank = r0 + r1 + r2 + r3;
+        for (int o = 1; o < P; o <<= 1) rank += __shfl_xor_sync(0xFFFFFFFFu, rank, o);
+        if (e < n && part == 0 && rank < nout) dst[rank] = key;
+    }
+}
+
+// Appends key(e) for every e in [0, L) with pred(e), in any order, to
+// dst[0..): a counting pass of warp ballots, a prefix over the warps'
+// counts, then a writing pass (no shared atomics).  L is a multiple of 256,
+// so every ballot covers a whole warp.  wsum: kSmallWarps + 1 words.
+template <typename Pr, typename Ky>
+__device__ __forceinline__ void small_append(int L, Pr pred, Ky key, uint64_t *dst, uint32_t *wsum) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t cnt = 0;
+    for (int e = tid; e < L; e += kSmallThreads) cnt += __popc(__ballot_sync(0xFFFFFFFFu, pred(e)));
+    if (lane == 0) wsum[warp] = cnt;
+    __syncthreads();
+    uint32_t pos = 0;
+    for (int w = 0; w < warp; ++w) pos += wsum[w];
+    const uint32_t below = (1u << lane) - 1u;
+    for (int e = tid; e < L; e += kSmallThreads) {
+        const bool keep = pred(e);
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+        if (keep) dst[pos + __popc(bal & below)] = key(e);
+        pos += __popc(bal);
+    }
+    __syncthreads();
+}
+
+// Ascending bitonic sort of keys[0..P), P a power of two.
+__device__ __forceinline__ void small_bitonic(uint64_t *keys, int P) {
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P / 2; i += kSmallThreads) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const uint64_t a = keys[lo], b = keys[hi];
+                if ((a > b) == asc) {
+                    keys[lo] = b;
+                    keys[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 __host__ __device__ constexpr size_t small_align_dev(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct SmallWS {
@@ -147,8 +222,7 @@ template <int MT>
 __global__ void __launch_bounds__(kSmallThreads, 2)
     topk_small_kernel(const uint32_t *__restrict__ codes, int64_t n, int32_t M, const uint8_t *__restrict__ luts,
                       int32_t k, int32_t metric, SmallWS ws, int nbc, int hshift,
-                      uint16_t *__restrict__ out_sums, int64_t *__restrict__ out_idx,
-                      const __grid_constant__ CUtensorMap lmap) {
+                      uint16_t *__restrict__ out_sums, int64_t *__restrict__ out_idx) {
     extern __shared__ __align__(128) uint8_t smem[];
     if (MT > 0) M = MT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -158,14 +232,17 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
     uint8_t *p = smem;
     uint32_t *hist = reinterpret_cast<uint32_t *>(p);
     p += kBins * 4;
-    uint32_t *misc = reinterpret_cast<uint32_t *>(p);  // [0..2) find results, [2] failed, [3] last, [8..) scan
+    // misc: [0..2) find results, [2] failure bits, [3] last CTA, [5] merge:
+    // total list entries, [6] merge: a list may hold more winners than its
+    // prefix, [7] merge: prefix keys, [8..) scan scratch
+    uint32_t *misc = reinterpret_cast<uint32_t *>(p);
     uint32_t *wsum = misc + 8;
     p += kSmallMiscWords * 4;
     uint4 *lut = reinterpret_cast<uint4 *>(p);
     p += (size_t)M * 16;
     uint64_t *bars = reinterpret_cast<uint64_t *>(p);
     const int nch = (nbc + kSmallChunk - 1) / kSmallChunk;
-    p += (size_t)((nch + 2) / 2 * 2) * 8;  // one barrier per chunk + the merge copy's
+    p += (size_t)((nch + 2) / 2 * 2) * 8;  // one barrier per chunk
     uint8_t *region = p;  // codes + sums during the scan; keys during the merge
     const uint32_t blk_bytes = (uint32_t)M * kRowBytes;
     uint32_t *codes_s = reinterpret_cast<uint32_t *>(region);
@@ -180,6 +257,9 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
         for (int c = 0; c < nchunks; ++c) mbar_init(&bars[c], 1);
         fence_mbar_init();
         misc[2] = 0;
+        misc[5] = 0;
+        misc[6] = 0;
+        misc[7] = 0;
         for (int c = 0; c < nchunks; ++c) {
             const int nbk = min(kSmallChunk, nblk - c * kSmallChunk);
             const uint32_t bytes = (uint32_t)nbk * blk_bytes;
@@ -189,8 +269,14 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
         }
     }
     for (int i = tid; i < kBins; i += kSmallThreads) hist[i] = 0;
+    // For dot the tables are complemented (255 - D is the byte complement),
+    // so the lookups produce s' = 255*M - S directly.
     const uint4 *lut_g = reinterpret_cast<const uint4 *>(luts + q * M * kK);
-    for (int i = tid; i < M; i += kSmallThreads) lut[i] = lut_g[i];
+    const uint32_t lut_x = metric == BOLT_METRIC_DOT ? 0xFFFFFFFFu : 0u;
+    for (int i = tid; i < M; i += kSmallThreads) {
+        const uint4 t = lut_g[i];
+        lut[i] = make_uint4(t.x ^ lut_x, t.y ^ lut_x, t.z ^ lut_x, t.w ^ lut_x);
+    }
     __syncthreads();
 
     const uint32_t smax = 255u * (uint32_t)M;
@@ -224,8 +310,7 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int i = 2 * h + j;
-                const uint32_t S = (w[h] >> (16 * j)) & 0xFFFFu;
-                uint32_t sp = metric == BOLT_METRIC_DOT ? smax - S : S;
+                uint32_t sp = (w[h] >> (16 * j)) & 0xFFFFu;
                 if (v0 + i >= n) sp = kPad;
                 else atomicAdd(&hist[sp >> hshift], 1u);
                 pair |= sp << (16 * j);
@@ -259,7 +344,7 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
         uint32_t below;
         const uint32_t B = small_find(hist, kk, misc, wsum, below);
         // The query's global histogram counts every CTA's kept keys: all of
-        // bins < B, and kk - below of bin B.
+        // bins < B, and kk - below of bin B (read by the merge's exact path).
         uint32_t *gh = ws.ghist + q * kBins;
         for (int b = tid; b <= (int)B; b += kSmallThreads) {
             const uint32_t c = b < (int)B ? hist[b] : kk - below;
@@ -282,15 +367,25 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
             c_lt = below + below2;
         }
         const int64_t base = b0 * kBlockVecs;
-        small_keep(L, T, kk - c_lt, s_of,
-                   [&](uint32_t pos, int e) { kept[pos] = ((uint64_t)sums_s[e] << 32) | (uint64_t)(base + e); },
-                   wsum);
-        // rank sort (keys are distinct): list position = number of smaller keys
-        for (int e = tid; e < (int)kk; e += kSmallThreads) {
-            const uint64_t key = kept[e];
-            int rank = 0;
-            for (int j = 0; j < (int)kk; ++j) rank += kept[j] < key ? 1 : 0;
-            mine[rank] = key;
+        // entries equal to T (the histogram still holds their count)
+        const uint32_t n_le = c_lt + hist[hshift > 0 ? (T & ((1u << hshift) - 1u)) : T];
+        // the code area is free now: room for nbc * M * 16 keys
+        const uint32_t cap_le = min((uint32_t)nbc * (uint32_t)M * 16u, kk + 64u);
+        if (n_le <= cap_le) {
+            // every entry with s' <= T (padding has s' = 0xFFFF > T) in any
+            // order; the rank sort keeps the kk smallest keys, which are the
+            // entries below T and the lowest indices among those equal to T
+            uint64_t *le = reinterpret_cast<uint64_t *>(region);
+            small_append(
+                L, [&](int e) { return (uint32_t)sums_s[e] <= T; },
+                [&](int e) { return ((uint64_t)sums_s[e] << 32) | (uint64_t)(base + e); }, le, wsum);
+            small_rank_sort(le, (int)n_le, mine, (int)kk);
+        } else {
+            // many entries equal to T: ordered compaction (lowest indices first)
+            small_keep(L, T, kk - c_lt, s_of,
+                       [&](uint32_t pos, int e) { kept[pos] = ((uint64_t)sums_s[e] << 32) | (uint64_t)(base + e); },
+                       wsum);
+            small_rank_sort(kept, (int)kk, mine, (int)kk);
         }
     }
     if (tid == 0) {
@@ -304,137 +399,194 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
     if (misc[3] == 0) return;
     __threadfence();
 
-    // ---- last CTA: merge the G sorted lists.  The histogram of all kept
-    // keys gives the k-th smallest s' of the union (T2) and the number below
-    // it (c2); each list then contributes a prefix: its keys below T2, and
-    // its keys equal to T2 while fewer than k - c2 such keys precede them in
-    // vector order (lists are in CTA order = vector order).  The first kp
-    // keys of every list come in with one 2-D tensor copy; keys past them
-    // (long prefixes: heavy ties) are read from global memory.
+    // ---- last CTA: merge the G sorted lists.  Fast path: the first kp keys
+    // of every list form a pool; its kout-th smallest s' is T*.  When every
+    // list longer than kp has its kp-th key above T*, no key past a prefix
+    // can be among the kout smallest (lists are sorted), so the pool's kout
+    // smallest keys are the answer.  Otherwise (a list holds more winners
+    // than its prefix) the exact path: the global histogram gives the kout-th
+    // smallest s' of the union (T2) and the number below it (c2); each list
+    // contributes a prefix found by binary search, ties at T2 taken in
+    // vector order (lists are in CTA order = vector order).
     const int kp = min(k, kSmallPrefix) + (min(k, kSmallPrefix) & 1);
     uint32_t *cnt_s = reinterpret_cast<uint32_t *>(region);  // [G] counts; then keys below T2
     uint32_t *lt_s = cnt_s + G;                              // [G] offsets of the keys below T2
     uint32_t *eq_s = lt_s + G;                               // [G] offsets of the keys equal to T2
-    // [G][kp], 128-byte aligned (tensor-copy destination)
+    // [G][kSmallPrefix]: the first kp keys of every list
     uint64_t *pre = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(region) + (size_t)G * 12 + 127) &
                                                  ~uintptr_t(127));
-    uint64_t *fin = pre + (size_t)G * kp;
-    const uint64_t *lists = ws.keys + q * qstride;
-    uint64_t *mbar = bars + nch;  // fresh barrier for the merge copies
-    if (tid == 0) {
-        mbar_init(mbar, 1);
-        fence_mbar_init();
-        // the lists and the histogram were written by other CTAs, and this
-        // CTA's shared memory was last used, through the generic proxy
-        asm volatile("fence.proxy.async;" ::: "memory");
-        mbar_arrive_expect_tx(mbar, (uint32_t)(G * kp * 8 + kBins * 4));
-        tma_load_2d(pre, &lmap, 0, (int)(q * G), mbar);
-        bulk_g2s(hist, ws.ghist + q * kBins, kBins * 4, mbar);
-    }
-    if (tid < G) cnt_s[tid] = __ldcg(ws.cnt + q * G + tid);
-    __syncthreads();
-    const bool copied = mbar_wait_bounded(mbar, 0u, kSmallWait);
-    if (!copied) atomicOr(&misc[2], 2u);
-    __syncthreads();
-    const bool qbad = (misc[2] & 2u) != 0u || __ldcg(&ws.status[q]) != 0u;
-    if (misc[2] & 2u) {
-        if (tid == 0) mbar_wait_bounded(mbar, 0u, kSmallWait / 10);  // bounded: let a late copy land
-        __syncthreads();
-    }
-    uint32_t total = 0;
-    small_scan(tid < G ? cnt_s[tid] : 0u, wsum, total);
-    const int kout = qbad ? 0 : (int)min((uint32_t)k, total);
-    auto key_at = [&](int c, uint32_t j) -> uint64_t {
-        return j < (uint32_t)kp ? pre[(size_t)c * kp + j] : __ldcg(lists + (int64_t)c * kslot + j);
-    };
-    // first position in list c whose s' >> sh is >= v (binary search; past
-    // the copied prefix only when the prefix's last key is below v)
-    auto lower = [&](int c, uint32_t v, int sh) -> uint32_t {
-        const uint32_t len = cnt_s[c];
-        uint32_t lo = 0, hi = min(len, (uint32_t)kp);
-        if (hi == (uint32_t)kp && hi < len && ((uint32_t)(pre[(size_t)c * kp + kp - 1] >> 32) >> sh) < v) {
-            lo = hi;
-            hi = len;
-        }
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (((uint32_t)(key_at(c, mid) >> 32) >> sh) < v) lo = mid + 1;
-            else hi = mid;
-        }
-        return lo;
-    };
-    if (kout > 0) {
-        uint32_t below;
-        const uint32_t B2 = small_find(hist, (uint32_t)kout, misc, wsum, below);
-        uint32_t T2 = B2, c2 = below;
-        if (hshift > 0) {  // exact value inside bin B2: count the bin's keys by value
-            const uint32_t mask = (1u << hshift) - 1u;
-            for (int i = tid; i < kBins; i += kSmallThreads) hist[i] = 0;
-            __syncthreads();
-            for (int c = warp; c < G; c += kSmallWarps) {
-                const uint32_t lo = lower(c, B2, hshift), hi = lower(c, B2 + 1, hshift);
-                for (uint32_t j = lo + lane; j < hi; j += 32)
-                    atomicAdd(&hist[(uint32_t)(key_at(c, j) >> 32) & mask], 1u);
-            }
-            __syncthreads();
-            uint32_t below2;
-            const uint32_t f = small_find(hist, (uint32_t)kout - below, misc, wsum, below2);
-            T2 = (B2 << hshift) | f;
-            c2 = below + below2;
-        }
-        const uint32_t r = (uint32_t)kout - c2;  // keys equal to T2 to keep, lowest index first
-        uint32_t lt = 0, eq = 0;
-        if (tid < G) {
-            lt = lower(tid, T2, 0);
-            eq = lower(tid, T2 + 1, 0) - lt;
-        }
-        uint32_t t1, t2;
-        const uint32_t lt_off = small_scan(lt, wsum, t1);
-        const uint32_t eq_off = small_scan(eq, wsum, t2);
-        if (tid < G) {
-            cnt_s[tid] = lt;  // the list's keys below T2 (its length is no longer needed)
-            lt_s[tid] = lt_off;
-            eq_s[tid] = eq_off;
-        }
-        __syncthreads();
-        for (int c = warp; c < G; c += kSmallWarps) {
-            const uint32_t nlt = cnt_s[c], lo = lt_s[c], eo = eq_s[c];
-            const uint32_t neq = eo < r ? min(r - eo, (c + 1 < G ? eq_s[c + 1] : t2) - eo) : 0u;
-            for (uint32_t j = lane; j < nlt; j += 32) fin[lo + j] = key_at(c, j);
-            for (uint32_t j = lane; j < neq; j += 32) fin[c2 + eo + j] = key_at(c, nlt + j);
-        }
-        __syncthreads();
-    }
-    // order the kout survivors by (s', index): rank counting for small k, bitonic otherwise
+    uint64_t *fin = pre + (size_t)G * kSmallPrefix;
+    constexpr int kPs = 4;  // log2(kSmallPrefix)
+    static_assert(kSmallPrefix == 1 << kPs, "prefix stride");
+    // pool entry e: key j = e mod 16 of list c = e / 16, valid while j is
+    // below the list's length (which is at most kp when kp < 16)
+    auto in_pool = [&](int e) { return (uint32_t)(e & (kSmallPrefix - 1)) < cnt_s[e >> kPs]; };
     int P = 1;
-    while (P < kout) P <<= 1;
-    if (kout <= 256) {
-        uint64_t *sorted = fin + P;
-        for (int e = tid; e < kout; e += kSmallThreads) {
-            const uint64_t key = fin[e];
-            int rank = 0;
-            for (int j = 0; j < kout; ++j) rank += fin[j] < key ? 1 : 0;
-            sorted[rank] = key;
+    while (P < k) P <<= 1;
+    const uint64_t *lists = ws.keys + q * qstride;
+    {
+        // list lengths (G <= kSmallThreads: one per thread), their total and
+        // the prefix keys' count: warp sums, then one shared add per warp
+        const uint32_t v = tid < G ? __ldcg(ws.cnt + q * G + tid) : 0u;
+        if (tid < G) cnt_s[tid] = v;
+        uint32_t tv = v, tp = min(v, (uint32_t)kp);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tv += __shfl_xor_sync(0xFFFFFFFFu, tv, o);
+            tp += __shfl_xor_sync(0xFFFFFFFFu, tp, o);
         }
-        __syncthreads();
-        fin = sorted;
-    } else {
-        for (int i = kout + tid; i < P; i += kSmallThreads) fin[i] = ~0ull;
-        __syncthreads();
-        for (int size = 2; size <= P; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = tid; i < P / 2; i += kSmallThreads) {
-                    const int lo = 2 * i - (i & (stride - 1));
-                    const int hi = lo + stride;
-                    const bool asc = (lo & size) == 0;
-                    const uint64_t a = fin[lo], b = fin[hi];
-                    if ((a > b) == asc) {
-                        fin[lo] = b;
-                        fin[hi] = a;
-                    }
+        if (lane == 0 && tv) {
+            atomicAdd(&misc[5], tv);
+            atomicAdd(&misc[7], tp);
+        }
+    }
+    {
+        // G * kSmallPrefix <= 256 * 16 slots: at most 8 per thread, all loads
+        // in flight at once (entries past a list's count are unused)
+        constexpr int kPerThread = 256 * kSmallPrefix / kSmallThreads;
+        uint64_t pv[kPerThread];
+#pragma unroll
+        for (int i = 0; i < kPerThread; ++i) {
+            const int e = tid + i * kSmallThreads, c = e >> kPs, j = e & (kSmallPrefix - 1);
+            pv[i] = c < G && j < kp ? __ldcg(lists + (int64_t)c * kslot + j) : 0ull;
+        }
+#pragma unroll
+        for (int i = 0; i < kPerThread; ++i) {
+            const int e = tid + i * kSmallThreads;
+            if (e < G * kSmallPrefix) pre[e] = pv[i];
+        }
+    }
+    if (tid == 0 && __ldcg(&ws.status[q]) != 0u) atomicOr(&misc[2], 4u);
+    for (int i = tid; i < kBins; i += kSmallThreads) hist[i] = 0;
+    __syncthreads();
+    const bool qbad = (misc[2] & 4u) != 0u;
+    const uint32_t total = misc[5];
+    const int kout = qbad ? 0 : (int)min((uint32_t)k, total);
+    bool sorted_done = false;
+    if (kout > 0) {
+        bool fast = misc[7] >= (uint32_t)kout;
+        uint32_t Tst = 0, n_le = 0;
+        if (fast) {
+            for (int e = tid; e < G * kSmallPrefix; e += kSmallThreads)
+                if (in_pool(e)) atomicAdd(&hist[(uint32_t)(pre[e] >> 32) >> hshift], 1u);
+            __syncthreads();
+            uint32_t below;
+            const uint32_t B = small_find(hist, (uint32_t)kout, misc, wsum, below);
+            Tst = B;
+            n_le = below + hist[B];
+            if (hshift > 0) {  // exact value inside bin B
+                const uint32_t mask = (1u << hshift) - 1u;
+                for (int i = tid; i < kBins; i += kSmallThreads) hist[i] = 0;
+                __syncthreads();
+                for (int e = tid; e < G * kSmallPrefix; e += kSmallThreads) {
+                    const uint32_t v = (uint32_t)(pre[e] >> 32);
+                    if (in_pool(e) && (v >> hshift) == B) atomicAdd(&hist[v & mask], 1u);
                 }
                 __syncthreads();
+                uint32_t below2;
+                const uint32_t f = small_find(hist, (uint32_t)kout - below, misc, wsum, below2);
+                Tst = (B << hshift) | f;
+                n_le = below + below2 + hist[f];
             }
+            for (int c = tid; c < G; c += kSmallThreads)
+                if (cnt_s[c] > (uint32_t)kp && (uint32_t)(pre[(size_t)c * kSmallPrefix + kp - 1] >> 32) <= Tst)
+                    atomicOr(&misc[6], 1u);
+            __syncthreads();
+            fast = misc[6] == 0u && n_le <= (uint32_t)P;
+        }
+        if (fast) {
+            // the pool's keys with s' <= T* (n_le of them), then the kout smallest
+            const int npool = (G * kSmallPrefix + 255) / 256 * 256;
+            small_append(
+                npool,
+                [&](int e) { return e < G * kSmallPrefix && in_pool(e) && (uint32_t)(pre[e] >> 32) <= Tst; },
+                [&](int e) { return pre[e]; }, fin, wsum);
+            if (kout <= 256) {
+                small_rank_sort(fin, (int)n_le, fin + P, kout);
+                __syncthreads();
+                fin += P;
+            } else {
+                for (int i = (int)n_le + tid; i < P; i += kSmallThreads) fin[i] = ~0ull;
+                __syncthreads();
+                small_bitonic(fin, P);
+            }
+            sorted_done = true;
+        } else {
+            // exact path: the global histogram of every list's keys
+            for (int i = tid; i < kBins; i += kSmallThreads) hist[i] = __ldcg(ws.ghist + q * kBins + i);
+            __syncthreads();
+            auto key_at = [&](int c, uint32_t j) -> uint64_t {
+                return j < (uint32_t)kp ? pre[(size_t)c * kSmallPrefix + j] : __ldcg(lists + (int64_t)c * kslot + j);
+            };
+            // first position in list c whose s' >> sh is >= v (binary search; past
+            // the prefix only when the prefix's last key is below v)
+            auto lower = [&](int c, uint32_t v, int sh) -> uint32_t {
+                const uint32_t len = cnt_s[c];
+                uint32_t lo = 0, hi = min(len, (uint32_t)kp);
+                if (hi == (uint32_t)kp && hi < len &&
+                    ((uint32_t)(pre[(size_t)c * kSmallPrefix + kp - 1] >> 32) >> sh) < v) {
+                    lo = hi;
+                    hi = len;
+                }
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (((uint32_t)(key_at(c, mid) >> 32) >> sh) < v) lo = mid + 1;
+                    else hi = mid;
+                }
+                return lo;
+            };
+            uint32_t below;
+            const uint32_t B2 = small_find(hist, (uint32_t)kout, misc, wsum, below);
+            uint32_t T2 = B2, c2 = below;
+            if (hshift > 0) {  // exact value inside bin B2: count the bin's keys by value
+                const uint32_t mask = (1u << hshift) - 1u;
+                for (int i = tid; i < kBins; i += kSmallThreads) hist[i] = 0;
+                __syncthreads();
+                for (int c = warp; c < G; c += kSmallWarps) {
+                    const uint32_t lo = lower(c, B2, hshift), hi = lower(c, B2 + 1, hshift);
+                    for (uint32_t j = lo + lane; j < hi; j += 32)
+                        atomicAdd(&hist[(uint32_t)(key_at(c, j) >> 32) & mask], 1u);
+                }
+                __syncthreads();
+                uint32_t below2;
+                const uint32_t f = small_find(hist, (uint32_t)kout - below, misc, wsum, below2);
+                T2 = (B2 << hshift) | f;
+                c2 = below + below2;
+            }
+            const uint32_t r = (uint32_t)kout - c2;  // keys equal to T2 to keep, lowest index first
+            uint32_t lt = 0, eq = 0;
+            if (tid < G) {
+                lt = lower(tid, T2, 0);
+                eq = lower(tid, T2 + 1, 0) - lt;
+            }
+            uint32_t t1, t2;
+            const uint32_t lt_off = small_scan(lt, wsum, t1);
+            const uint32_t eq_off = small_scan(eq, wsum, t2);
+            if (tid < G) {
+                cnt_s[tid] = lt;  // the list's keys below T2 (its length is no longer needed)
+                lt_s[tid] = lt_off;
+                eq_s[tid] = eq_off;
+            }
+            __syncthreads();
+            for (int c = warp; c < G; c += kSmallWarps) {
+                const uint32_t nlt = cnt_s[c], lo = lt_s[c], eo = eq_s[c];
+                const uint32_t neq = eo < r ? min(r - eo, (c + 1 < G ? eq_s[c + 1] : t2) - eo) : 0u;
+                for (uint32_t j = lane; j < nlt; j += 32) fin[lo + j] = key_at(c, j);
+                for (uint32_t j = lane; j < neq; j += 32) fin[c2 + eo + j] = key_at(c, nlt + j);
+            }
+            __syncthreads();
+        }
+    }
+    if (kout > 0 && !sorted_done) {
+        // order the kout survivors of the exact path by (s', index)
+        if (kout <= 256) {
+            small_rank_sort(fin, kout, fin + P, kout);
+            __syncthreads();
+            fin += P;
+        } else {
+            for (int i = kout + tid; i < P; i += kSmallThreads) fin[i] = ~0ull;
+            __syncthreads();
+            small_bitonic(fin, P);
         }
     }
     for (int r = tid; r < k; r += kSmallThreads) {
@@ -459,7 +611,7 @@ bool plan_topk_small(int64_t n, int32_t M, int32_t k, int sms, TopkPlan *plan) {
     int64_t G = sms;
     if (G > nb) G = nb;
     if (G > kSmallMergeKeys / k) G = kSmallMergeKeys / k;
-    if (G > 256) G = 256;  // tensor-map box rows
+    if (G > 256) G = 256;  // the merge's exact path takes one list per thread
     if (G < 1) return false;
     const int64_t nbc = (nb + G - 1) / G;
     G = (nb + nbc - 1) / nbc;  // every CTA gets at least one block
@@ -468,8 +620,7 @@ bool plan_topk_small(int64_t n, int32_t M, int32_t k, int sms, TopkPlan *plan) {
     const int nch = (int)((nbc + kSmallChunk - 1) / kSmallChunk);
     const size_t scan_region = small_align((size_t)nbc * M * kRowBytes + (size_t)nbc * kBlockVecs * 2, 16) +
                                (size_t)k * 8;
-    const size_t kp = (size_t)((k < kSmallPrefix ? k : kSmallPrefix) + ((k < kSmallPrefix ? k : kSmallPrefix) & 1));
-    const size_t merge_region = (size_t)G * 12 + 128 + (size_t)G * kp * 8 + (size_t)2 * P * 8;
+    const size_t merge_region = (size_t)G * 12 + 128 + (size_t)G * kSmallPrefix * 8 + (size_t)2 * P * 8;
     const size_t region = scan_region > merge_region ? scan_region : merge_region;
     const size_t smem = (size_t)kBins * 4 + kSmallMiscWords * 4 + small_align((size_t)M * 16, 16) +
                         (size_t)((nch + 2) / 2 * 2) * 8 + region;
@@ -502,25 +653,9 @@ static int launch_small_w(const uint8_t *codes, int64_t n, int32_t M, const uint
     auto kern = topk_small_kernel<MT>;
     int rc = ensure_smem((const void *)kern, plan.smem_bytes);
     if (rc) return rc;
-    // the slot lists as a 2-D tensor {kslot, G * nq} of 64-bit keys; the
-    // merge copies the box of the first kp keys of all G lists of a query
-    auto enc = tensor_map_encoder();
-    BOLT_REQUIRE(enc, BOLT_ECUDA, "cuTensorMapEncodeTiled is unavailable");
-    const int kslot = k + (k & 1);
-    const int kp = (k < kSmallPrefix ? k : kSmallPrefix) + ((k < kSmallPrefix ? k : kSmallPrefix) & 1);
-    CUtensorMap lmap;
-    const cuuint64_t dims[2] = {(cuuint64_t)kslot, (cuuint64_t)plan.grid * (cuuint64_t)nq};
-    const cuuint64_t strides[1] = {(cuuint64_t)kslot * 8};
-    const cuuint32_t box[2] = {(cuuint32_t)kp, (cuuint32_t)plan.grid};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = enc(&lmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, w.keys, dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    BOLT_REQUIRE(r == CUDA_SUCCESS, BOLT_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     dim3 grid(plan.grid, (unsigned)nq);
     kern<<<grid, kSmallThreads, plan.smem_bytes, stream>>>(reinterpret_cast<const uint32_t *>(codes), n, M, luts, k,
-                                                            metric, w, plan.nbc, plan.hshift, out_sums, out_idx,
-                                                            lmap);
+                                                            metric, w, plan.nbc, plan.hshift, out_sums, out_idx);
     return check_launch("topk_small_kernel");
 }
 

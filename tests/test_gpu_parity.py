@@ -199,7 +199,7 @@ def check_topk(torch, codes, luts, k, metric, workspace=None):
                                    (1539, 16, 10), (100_003, 16, 100), (25_603, 8, 64),
                                    (200_000, 8, 100), (50_000, 32, 1000), (20_000, 64, 50), (3000, 128, 20),
                                    (600, 256, 5), (6_000_000, 16, 100), (3_000_000, 32, 10),
-                                   (2_600_000, 8, 1024), (400_000, 64, 50)])
+                                   (2_600_000, 8, 1024), (400_000, 64, 50), (200_000, 16, 300)])
 def test_topk_bitexact(torch_cuda, metric, n, M, k):
     rng = np.random.default_rng(n * 7 + M + k + metric)
     codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
@@ -244,6 +244,21 @@ def test_topk_heavy_ties(torch_cuda, metric):
     check_topk(torch_cuda, codes, luts, 100, metric)
     luts0 = np.zeros((1, M, 16), np.uint8)  # every sum equal
     check_topk(torch_cuda, codes, luts0, 64, metric)
+
+
+@pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
+def test_topk_small_class_winners_in_one_range(torch_cuda, metric):
+    """Shared-memory size class with the best sums all in the first rows
+    (rows ordered by their sum under the query's tables): the first CTA's list
+    holds every winner, more than the merge's 16-key prefix, so the merge
+    takes its exact path (global histogram, searches past the prefix)."""
+    rng = np.random.default_rng(11 + metric)
+    n, M, k = 100_003, 16, 100
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+    luts = rng.integers(0, 256, (2, M, 16)).astype(np.uint8)
+    S = luts[0][np.arange(M)[None, :], codes].astype(np.int64).sum(axis=1)
+    order = np.argsort(S if metric == bolt.METRIC_L2 else -S, kind="stable")
+    check_topk(torch_cuda, codes[order], luts, k, metric)
 
 
 def test_topk_sorted_input_worst_case(torch_cuda):
