@@ -80,16 +80,24 @@ __device__ __forceinline__ uint32_t small_scan(uint32_t v, uint32_t *wsum, uint3
 // kk <= total are required.
 __device__ __forceinline__ uint32_t small_find(const uint32_t *hist, uint32_t kk, uint32_t *misc, uint32_t *wsum,
                                                uint32_t &below) {
-    constexpr int BPT = kBins / kSmallThreads;  // 8
-    const int tid = threadIdx.x;
-    uint32_t v[BPT], local = 0;
+    constexpr int BPT = kBins / kSmallThreads;  // 8: two 16-byte loads per thread
+    static_assert(BPT == 8, "bins per thread");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint4 a = reinterpret_cast<const uint4 *>(hist)[2 * tid], b = reinterpret_cast<const uint4 *>(hist)[2 * tid + 1];
+    const uint32_t v[BPT] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t local = 0;
 #pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        v[i] = hist[tid * BPT + i];
-        local += v[i];
+    for (int i = 0; i < BPT; ++i) local += v[i];
+    uint32_t incl = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += t;
     }
-    uint32_t total;
-    const uint32_t excl = small_scan(local, wsum, total);
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t excl = incl - local;
+    for (int w = 0; w < warp; ++w) excl += wsum[w];
     if (excl < kk && kk <= excl + local) {
         uint32_t c = excl;
 #pragma unroll
@@ -103,9 +111,9 @@ __device__ __forceinline__ uint32_t small_find(const uint32_t *hist, uint32_t kk
     }
     __syncthreads();
     below = misc[1];
-    const uint32_t b = misc[0];
+    const uint32_t bin = misc[0];
     __syncthreads();
-    return b;
+    return bin;
 }
 
 // Ordered compaction: entry e (vector order) is kept if s' < T, or s' == T
@@ -139,16 +147,17 @@ __device__ __forceinline__ void small_keep(int L, uint32_t T, uint32_t r, F s, E
 }
 
 // Of the n distinct keys of src (shared memory), writes those of rank < nout
-// to dst[rank] (increasing order): each key's rank is the number of smaller
-// keys, counted by P adjacent threads per key.
-__device__ __forceinline__ void small_rank_sort(const uint64_t *src, int n, uint64_t *dst, int nout) {
+// to dst[rank] as expand(key) (increasing order): each key's rank is the
+// number of smaller keys, counted by P adjacent threads per key.
+template <typename K, typename X>
+__device__ __forceinline__ void small_rank_sort(const K *src, int n, uint64_t *dst, int nout, X expand) {
     const int tid = threadIdx.x;
     int P = 1;
     while (P < 32 && n * P * 2 <= kSmallThreads) P <<= 1;
     const int part = tid & (P - 1);
     for (int base = 0; base < n; base += kSmallThreads / P) {
         const int e = base + tid / P;
-        const uint64_t key = e < n ? src[e] : ~0ull;
+        const K key = e < n ? src[e] : K(0);
         int r0 = 0, r1 = 0, r2 = 0, r3 = 0;
         if (e < n) {
             int j = part;
@@ -162,8 +171,51 @@ __device__ __forceinline__ void small_rank_sort(const uint64_t *src, int n, uint
         }
         int rank = r0 + r1 + r2 + r3;
         for (int o = 1; o < P; o <<= 1) rank += __shfl_xor_sync(0xFFFFFFFFu, rank, o);
-        if (e < n && part == 0 && rank < nout) dst[rank] = key;
+        if (e < n && part == 0 && rank < nout) dst[rank] = expand(key);
     }
+}
+
+__device__ __forceinline__ void small_rank_sort(const uint64_t *src, int n, uint64_t *dst, int nout) {
+    small_rank_sort(src, n, dst, nout, [](uint64_t key) { return key; });
+}
+
+// Entries e < L of the CTA's sums (uint16 in vector order, padding 0xFFFF)
+// with s' <= T, as 32-bit keys (s' << 16 | e) in any order: one count pass
+// over 16-byte chunks, a prefix over threads, one writing pass.  L is a
+// multiple of 8 and at most 65536.  wsum: kSmallWarps words.
+__device__ __forceinline__ void small_keep_le(const uint16_t *sums, int L, uint32_t T, uint32_t *dst,
+                                              uint32_t *wsum) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(sums);
+    const int nc = L >> 3;
+    uint32_t cnt = 0;
+    for (int c = tid; c < nc; c += kSmallThreads) {
+        const uint4 w = s4[c];
+        const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) cnt += ((x[i] & 0xFFFFu) <= T ? 1u : 0u) + ((x[i] >> 16) <= T ? 1u : 0u);
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t pos = incl - cnt;
+    for (int w = 0; w < warp; ++w) pos += wsum[w];
+    for (int c = tid; c < nc; c += kSmallThreads) {
+        const uint4 w = s4[c];
+        const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t lo = x[i] & 0xFFFFu, hi = x[i] >> 16, e = (uint32_t)c * 8u + 2u * i;
+            if (lo <= T) dst[pos++] = (lo << 16) | e;
+            if (hi <= T) dst[pos++] = (hi << 16) | (e + 1u);
+        }
+    }
+    __syncthreads();
 }
 
 // Appends key(e) for every e in [0, L) with pred(e), in any order, to
@@ -369,17 +421,18 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
         const int64_t base = b0 * kBlockVecs;
         // entries equal to T (the histogram still holds their count)
         const uint32_t n_le = c_lt + hist[hshift > 0 ? (T & ((1u << hshift) - 1u)) : T];
-        // the code area is free now: room for nbc * M * 16 keys
-        const uint32_t cap_le = min((uint32_t)nbc * (uint32_t)M * 16u, kk + 64u);
-        if (n_le <= cap_le) {
+        // the code area is free now: room for nbc * M * 32 keys of 32 bits
+        const uint32_t cap_le = min((uint32_t)nbc * (uint32_t)M * 32u, kk + 64u);
+        if (n_le <= cap_le && L <= 65536) {
             // every entry with s' <= T (padding has s' = 0xFFFF > T) in any
-            // order; the rank sort keeps the kk smallest keys, which are the
-            // entries below T and the lowest indices among those equal to T
-            uint64_t *le = reinterpret_cast<uint64_t *>(region);
-            small_append(
-                L, [&](int e) { return (uint32_t)sums_s[e] <= T; },
-                [&](int e) { return ((uint64_t)sums_s[e] << 32) | (uint64_t)(base + e); }, le, wsum);
-            small_rank_sort(le, (int)n_le, mine, (int)kk);
+            // order as (s' << 16 | e); the rank sort keeps the kk smallest
+            // keys, which are the entries below T and the lowest indices
+            // among those equal to T
+            uint32_t *le = reinterpret_cast<uint32_t *>(region);
+            small_keep_le(sums_s, L, T, le, wsum);
+            small_rank_sort(le, (int)n_le, mine, (int)kk, [&](uint32_t key) {
+                return ((uint64_t)(key >> 16) << 32) | (uint64_t)(base + (int64_t)(key & 0xFFFFu));
+            });
         } else {
             // many entries equal to T: ordered compaction (lowest indices first)
             small_keep(L, T, kk - c_lt, s_of,
