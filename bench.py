@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--graph-reps", type=int, default=0, help="also time graph replays of the launches")
     ap.add_argument("--collections", type=int, default=64, help="--only batch: first N collections")
     ap.add_argument("--topk-streams", type=int, default=8, help="streams of the 1M step's one-query launches")
-    ap.add_argument("--large-streams", type=int, default=2, help="streams of the 50M step's one-query launches")
+    ap.add_argument("--large-streams", type=int, default=4, help="streams of the 50M step's one-query launches")
     ap.add_argument("--large-nq", type=int, default=64, help="queries per metric in the 50M step")
     return ap.parse_args()
 
@@ -818,10 +818,10 @@ def approx_matmul_standalone(hbm_peak):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one topk_kernel launch
-# (ncu, one query, 8,000,000 vectors, cold caches: 64,114,176 + 25,856
+# (ncu, one query, 8,000,000 vectors, cold caches: 64,133,888 + 11,264
 # bytes, profiles/topk_kernel_mixture_8m.md) scaled by 50M / 8M; the traffic
 # is the codes once, proportional to n.  None once the kernel changes.
-TOPK_TRAFFIC_50M = (64_114_176 + 25_856) * 50 // 8
+TOPK_TRAFFIC_50M = (64_133_888 + 11_264) * 50 // 8
 
 
 def roofline_topk_50m(launch_ms, n, M, hbm_peak, peak_kind, core_us):

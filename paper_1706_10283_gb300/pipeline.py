@@ -14,7 +14,10 @@ and runs, in order (all in libbolt.so kernels):
 The launch sequence is captured once into a CUDA graph and replayed, so the
 per-launch host overhead of the thousands of small launches is paid once.
 ``run_from_host`` adds the host->device copy of the step's inputs from pinned
-memory and the device->host copy of its results.
+memory and the device->host copy of its results; the upload runs on its own
+stream and waits only until the previous step's encode and table build have
+read the input buffers, so consecutive steps overlap one step's upload with
+the previous step's searches.
 """
 import numpy as np
 import torch
@@ -57,12 +60,19 @@ class SearchStep:
         self.ws = [torch.empty(bolt.topk_workspace_bytes(n, M, 1, k), dtype=torch.uint8, device=dev)
                    for _ in self.side]
         self.graphs = None
+        self.copy_stream = torch.cuda.Stream(device=dev)
+        self._copied = torch.cuda.Event()
+        # recorded on the current stream after every write or read of X and Q
+        # there (set_inputs, the encode and table build of a replay): an
+        # upload into X and Q waits for it
+        self._inputs_read = torch.cuda.Event()
         self.launches_per_step = 1 + len(self.metrics) * (2 + nq)
         self.timing = []  # (start, end) event pairs around each top-k segment
 
     def set_inputs(self, X, Q):
         self.X.copy_(X)
         self.Q.copy_(Q)
+        self._inputs_read.record()
 
     # The step in three kinds of segments, so that top-k launches can be timed
     # by ordinary stream events recorded between graph replays.
@@ -117,6 +127,7 @@ class SearchStep:
         if self.graphs is None:
             self.capture()
         self.graphs[0].replay()
+        self._inputs_read.record()  # the encode and tables have read X and Q
         for g in self.graphs[1:-1]:
             if timed:
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -188,9 +199,21 @@ class SearchStep:
         return tot / (len(self.timing) * self.nq)
 
     def run_from_host(self, X_host, Q_host, out_idx_host, out_dist_host):
-        """End to end: pinned host inputs -> device step -> host results."""
-        self.X.copy_(X_host, non_blocking=True)
-        self.Q.copy_(Q_host, non_blocking=True)
+        """End to end: pinned host inputs -> device step -> host results
+        (asynchronous; X_host and Q_host must stay unchanged, and the host
+        outputs unread, until the current stream reaches this point).  The
+        upload goes on copy_stream after the previous step's encode and
+        tables have read the input buffers, so it overlaps that step's
+        searches; the step itself waits for the upload."""
+        cur = torch.cuda.current_stream()
+        if self.graphs is None:
+            self.capture()
+        self.copy_stream.wait_event(self._inputs_read)
+        with torch.cuda.stream(self.copy_stream):
+            self.X.copy_(X_host, non_blocking=True)
+            self.Q.copy_(Q_host, non_blocking=True)
+            self._copied.record(self.copy_stream)
+        cur.wait_event(self._copied)
         self.replay()
         for j, m in enumerate(self.metrics):
             out_idx_host[j].copy_(self.idx[m], non_blocking=True)

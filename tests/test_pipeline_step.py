@@ -7,7 +7,7 @@ replays, and through run_from_host (pinned host buffers in and out).
 Two configurations: the shared-memory size class on a mixture database
 with 8 streams (the 1,000,000-vector step's form, at 262,147 vectors), and
 the 50,000,000-vector resident database with a 1,000,064-row insert batch
-encoded into its last rows each step, on 2 streams (the headline step).
+encoded into its last rows each step, on 4 streams (the headline step).
 """
 import numpy as np
 import pytest
@@ -97,12 +97,14 @@ def clustered_codes(n, M, seed, clusters=256, chunk=5_000_000):
     return out
 
 
-def test_search_step_50m_insert_two_streams(torch_cuda):
+def test_search_step_50m_insert_four_streams(torch_cuda):
     """The headline step at full size: 50,000,000 resident codes, the insert
     batch of 1,000,064 mixture rows encoded into rows 48,999,936 .. 50M each
-    step, L2 and dot tables, one-query top-100 launches alternating on 2
+    step, L2 and dot tables, one-query top-100 launches round-robin on 4
     streams, dequantize; 3 graph replays, then every query against the
-    oracle over the whole database (its last rows re-encoded by the oracle)."""
+    oracle over the whole database (its last rows re-encoded by the oracle),
+    then two end-to-end steps from pinned host buffers back to back (the
+    second step's upload overlaps the first step's searches)."""
     torch = torch_cuda
     cfg = synth.CONFIGS["serve_50m"]
     n, J, M, k, nq = cfg["n"], cfg["J"], cfg["M"], 100, 6
@@ -118,7 +120,7 @@ def test_search_step_50m_insert_two_streams(torch_cuda):
     Xins = synth.mixture(nx, J, 52)
     Q = synth.mixture(nq, J, 53)
     dcodes = bolt.pack_codes(torch.from_numpy(codes).cuda())
-    step = SearchStep(n, J, M, nq, k, torch.from_numpy(C).cuda(), quant, streams=2, codes=dcodes,
+    step = SearchStep(n, J, M, nq, k, torch.from_numpy(C).cuda(), quant, streams=4, codes=dcodes,
                       insert_row0=row0, insert_rows=nx)
     step.set_inputs(torch.from_numpy(Xins).cuda(), torch.from_numpy(Q).cuda())
     step.capture()
@@ -133,7 +135,14 @@ def test_search_step_50m_insert_two_streams(torch_cuda):
     check_step(torch, step, want)
     oi = [torch.full((nq, k), -7, dtype=torch.int64).pin_memory() for _ in step.metrics]
     od = [torch.zeros((nq, k), dtype=torch.float32).pin_memory() for _ in step.metrics]
-    step.run_from_host(torch.from_numpy(Xins).pin_memory(), torch.from_numpy(Q).pin_memory(), oi, od)
+    # a first step from other inputs, then the checked one: its upload may
+    # start while the first step's searches run, never before its encode
+    Xh, Qh = torch.from_numpy(Xins).pin_memory(), torch.from_numpy(Q).pin_memory()
+    Xz, Qz = torch.zeros_like(Xh).pin_memory(), torch.zeros_like(Qh).pin_memory()
+    oz = [torch.empty_like(t).pin_memory() for t in oi]
+    dz = [torch.empty_like(t).pin_memory() for t in od]
+    step.run_from_host(Xz, Qz, oz, dz)
+    step.run_from_host(Xh, Qh, oi, od)
     torch.cuda.synchronize()
     for j, m in enumerate(step.metrics):
         np.testing.assert_array_equal(oi[j].numpy(), want[m][2])
