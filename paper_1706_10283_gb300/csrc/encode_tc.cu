@@ -213,6 +213,14 @@ __device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t par, volatile ui
     return true;
 }
 
+// Approximate square root (the hardware instruction; relative error far
+// below the 1e-4 slack the margin adds).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Canonical fp32 distance of x's subvector (s contiguous floats in global
 // memory) to one centroid c.
 __device__ __forceinline__ float canon_dist_g(const float *__restrict__ x, const float *__restrict__ c, int s) {
@@ -439,6 +447,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         constexpr int QB = 1;  // chunks per iteration
         const int i0 = part * PP;            // this part's first subspace of a chunk
         const bool has_work = i0 < SH::SPC;
+        // tile and chunk of q0, advanced with q0 (no divisions in the loop)
+        int64_t t_cur = blockIdx.x;
+        int c_cur = 0;
         for (uint32_t q0 = 0; q0 < total; q0 += QB) {
             const uint32_t nq = min((uint32_t)QB, total - q0);
             bool ok = true;
@@ -464,12 +475,13 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 for (int j = 0; j < QB; ++j)
 #pragma unroll
                     for (int ii = 0; ii < PP; ++ii) tmem_wait_ld(d[j][ii]);
+                static_assert(QB == 1, "one chunk per epilogue iteration");
 #pragma unroll
                 for (int j = 0; j < QB; ++j) {
                     if ((uint32_t)j >= nq) break;
                     const uint32_t q = q0 + j, bb = q % NB;
-                    const int64_t t = q_tile(q);
-                    const int c = (int)(q % nchunks);
+                    const int64_t t = t_cur;
+                    const int c = c_cur;
                     const int64_t v = t * kTcRows + r;
                     const bool valid = v < n;
 #pragma unroll
@@ -486,11 +498,15 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                             sc[4 * k4 + 2] = __fmaf_rn(-2.0f, d[j][ii][4 * k4 + 2], cc.z);
                             sc[4 * k4 + 3] = __fmaf_rn(-2.0f, d[j][ii][4 * k4 + 3], cc.w);
                         }
-                        float best = sc[0];
+                        // minimum as a tree (fminf is exact: any order gives the same value)
+                        float mn[8];
 #pragma unroll
-                        for (int k = 1; k < 16; ++k) best = fminf(best, sc[k]);
+                        for (int k = 0; k < 8; ++k) mn[k] = fminf(sc[k], sc[k + 8]);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) mn[k] = fminf(mn[k], mn[k + 4]);
+                        const float best = fminf(fminf(mn[0], mn[2]), fminf(mn[1], mn[3]));
                         // margin 4 (eps + eta) as a quadratic in X with per-codebook coefficients
-                        const float Xn = sqrtf(nrm[((size_t)bb * SH::SPC + i) * kTcRows + r]) * 1.0001f + 1e-30f;
+                        const float Xn = sqrt_approx(nrm[((size_t)bb * SH::SPC + i) * kTcRows + r]) * 1.0001f + 1e-30f;
                         const float4 pc = reinterpret_cast<const float4 *>(cmax)[m];
                         const float lim = best + __fmaf_rn(__fmaf_rn(pc.z, Xn, pc.y), Xn, pc.x);
                         uint32_t mask = 0;
@@ -530,13 +546,17 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     mbar_arrive(&bars[kBarAccFree + bb]);
                     mbar_arrive(&bars[kBarNFree + bb]);
                 }
-                const int64_t t = q_tile(q);
-                const int c = (int)(q % nchunks);
+                const int64_t t = t_cur;
+                const int c = c_cur;
                 if (pad_writer && t == ntiles - 1 && c == nchunks - 1 && ((t + 1) * kTcRows) % kBlockVecs != 0) {
                     // second half of the last block holds padding vectors: code 0
                     const int64_t blk = (t * kTcRows) >> 8;
                     for (int ee = lane; ee < M * 16; ee += 32)
                         codes[(blk * M + ee / 16) * kRowWords + 16 + (ee % 16)] = 0u;
+                }
+                if (++c_cur == nchunks) {
+                    c_cur = 0;
+                    t_cur += gridDim.x;
                 }
             }
         }

@@ -4,7 +4,9 @@
 and runs, in order (all in libbolt.so kernels):
   1. encode the database (Sec. 3.1 h, K = 16) -- or, for a resident database
      passed in as ``codes``, encode a batch of ``insert_rows`` new vectors
-     into rows ``insert_row0 ..`` of it (an online insert, Sec. 1.3),
+     into rows ``insert_row0 ..`` of it (an online insert, Sec. 1.3); by
+     default on the tensor cores (bf16 split operands, fp32 accumulation and
+     an fp32 re-check of near ties: the same codes as the fp32 encoder),
   2. build the uint8 query tables for each metric (Sec. 3.1 g, Sec. 3.2 beta),
   3. scan + exact top-k, one query per launch (the plain GPU form); the
      launches go round-robin to ``streams`` CUDA streams, each with its own
@@ -27,7 +29,8 @@ from . import bolt
 
 class SearchStep:
     def __init__(self, n, J, M, nq, k, centroids, quant, metrics=(bolt.METRIC_L2, bolt.METRIC_DOT),
-                 precision=bolt.PREC_FP32, device="cuda", streams=8, codes=None, insert_row0=0, insert_rows=None):
+                 precision=bolt.PREC_BF16_RECHECK, device="cuda", streams=8, codes=None, insert_row0=0,
+                 insert_rows=None):
         self.n, self.J, self.M, self.nq, self.k = n, J, M, nq, k
         self.metrics = tuple(metrics)
         self.quant = dict(quant)  # metric -> (a, b)
