@@ -60,6 +60,10 @@ extern "C" {
 #define BOLT_METRIC_L1 2  /* delta = absolute difference, f = identity: the L_p family of
                              Sec. 1.1 with p = 1 (f = r^(1/p) is monotone, so top-k ranks
                              by the sum, ascending, as for L2) */
+#define BOLT_METRIC_LP 3  /* delta = |difference|^p for a real p > 0 (tables built by
+                             bolt_build_luts_lp): the L_p family of Sec. 1.1; top-k ranks by
+                             the sum, ascending.  Accepted by the top-k, merge and filter
+                             calls; the tables come from the _lp entry points */
 
 #define BOLT_PREC_FP32 0         /* canonical fp32 encoder */
 #define BOLT_PREC_BF16_RECHECK 1 /* tensor-core bf16 scores + fp32 re-check */
@@ -123,6 +127,19 @@ int bolt_build_luts(const float *Q, int64_t nq, int32_t J, int32_t M,
                     const float *centroids, int32_t metric, float a,
                     const float *b_host, uint8_t *luts, float *luts_f32,
                     void *stream);
+
+/* L_p tables for a real exponent p > 0 (the d = f(sum delta) family of
+ * Sec. 1.1 with delta = |q_j - c_j|^p): D[q][m][k] = sum over the dims of
+ * subspace m, in order from the first, of powf(|q_j - c_kj|, p) (CUDA's
+ * powf, fp32 adds), then quantized by beta_m exactly as bolt_build_luts
+ * does.  The fp32 entries follow the library powf, whose results can differ
+ * from another implementation's in the last bits.  Same arguments as
+ * bolt_build_luts otherwise (M up to 4096); rank the sums with
+ * BOLT_METRIC_LP.  BOLT_EINVAL unless p > 0 and finite. */
+int bolt_build_luts_lp(const float *Q, int64_t nq, int32_t J, int32_t M,
+                       const float *centroids, float p, float a,
+                       const float *b_host, uint8_t *luts, float *luts_f32,
+                       void *stream);
 
 /* ---------------------------------------------------------------- scan d^
  * Sec. 3.1 approximate distance: sums[q][i] = sum_m luts[q][m][code_m(x_i)],
@@ -224,15 +241,22 @@ int bolt_topk_noalloc(const uint8_t *codes, int64_t n, int32_t M, const uint8_t 
  * One bolt_collection per collection; all pointers are device memory:
  *   codes : blocked layout of n vectors and M codebooks (16-byte aligned)
  *   luts  : nq x M x 16 uint8 tables (16-byte aligned)
- *   sums  : nq rows of ld uint16, sums[q * ld + i] for i < n (16-byte
- *           aligned; ld >= n and a multiple of 8).  Entries i in [n, ld) of
- *           each row may be overwritten with padding sums.
+ *   sums  : nq rows of ld sums, sums[q * ld + i] for i < n (16-byte
+ *           aligned; ld >= n and a multiple of 8), uint16 or, with
+ *           sum_bits = 32, uint32 (pass the uint32 buffer cast to uint16_t*).
+ *           Entries i in [n, ld) of each row may be overwritten with padding
+ *           sums.
  *   n, nq : sizes (either may be 0: the collection then has no work)
- *   M     : 1 <= M <= 256
+ *   M     : 1 <= M <= 256 with uint16 sums; up to 4096 with uint32 sums
+ *           (codebooks summed in groups of 256, each group exact in 16 bits)
  *   qt_max: queries one warp accumulates in registers per pass over a code
  *           block: 1, 2, 4, 8 or 16; 0 = library default (8)
  *   units_per_warp: (block, query-tile) units each warp of a CTA takes per
  *           task, 1..64; 0 = library default (4)
+ *   sum_bits: 0 or 16 = uint16 sums, 32 = uint32 sums (any M; required for
+ *           M > 256, where a uint16 sum could overflow); uint32 collections
+ *           take at most 2 queries per pass, and above 1024 codebooks read
+ *           their tables from global memory instead of staging them
  * qt_max and units_per_warp change speed only, never results;
  * bolt_batch_autotune chooses them by timing. */
 typedef struct bolt_collection {
@@ -245,7 +269,7 @@ typedef struct bolt_collection {
     int32_t M;
     int32_t qt_max;
     int32_t units_per_warp;
-    int32_t reserved; /* must be 0 */
+    int32_t sum_bits; /* 0 or 16: uint16 sums; 32: uint32 sums */
 } bolt_collection;
 
 /* Bytes of device memory the plan for these collections needs (host only;
@@ -367,6 +391,11 @@ int bolt_fit_codebooks(const float *X, int64_t n, int32_t J, int32_t M,
 int bolt_fit_quantizer(const float *Qtrain, int64_t nqt, int32_t J, int32_t M,
                        const float *centroids, int32_t metric, float *a_host,
                        float *b_host, int32_t *alpha_idx_host, void *stream);
+
+/* The same fit over the L_p tables of bolt_build_luts_lp (exponent p > 0). */
+int bolt_fit_quantizer_lp(const float *Qtrain, int64_t nqt, int32_t J, int32_t M,
+                          const float *centroids, float p, float *a_host,
+                          float *b_host, int32_t *alpha_idx_host, void *stream);
 
 /* ---------------------------------------------------------------- timeout-path tests
  * Sets the time limit, in nanoseconds, of the waits of the streaming top-k

@@ -29,6 +29,7 @@ from . import build as _build
 METRIC_L2 = 0
 METRIC_DOT = 1
 METRIC_L1 = 2
+METRIC_LP = 3  # |q - c|^p tables (lut_lp_f32 / lut_lp_f64), ranked ascending
 K = 16
 ALPHAS = (0.0, 0.001, 0.002, 0.005, 0.01, 0.02, 0.05, 0.1)
 
@@ -55,6 +56,8 @@ def lib():
             "bo_kmeans": [f32p, i64, i32, i32, i32, i64p, f32p, C.c_void_p],
             "bo_lut_f32": [f32p, i64, i32, i32, f32p, i32, f32p],
             "bo_lut_f64": [f32p, i64, i32, i32, f32p, i32, f64p],
+            "bo_lut_lp_f32": [f32p, i64, i32, i32, f32p, C.c_float, f32p],
+            "bo_lut_lp_f64": [f32p, i64, i32, i32, f32p, C.c_float, f64p],
             "bo_quantize": [f32p, i64, i32, f32, f32p, u8p],
             "bo_quant_params": [f32p, i64, i32, i32, C.POINTER(C.c_double), f64p],
             "bo_fit_quant": [f32p, i64, i32, C.POINTER(C.c_float), f32p, C.POINTER(C.c_int32), f64p],
@@ -143,6 +146,26 @@ def lut_f64(Q, C_, metric):
     M = C_.shape[0]
     D = np.empty((nq, M, K), np.float64)
     _ok(lib().bo_lut_f64(Q, nq, J, M, C_, metric, D), "lut_f64")
+    return D
+
+
+def lut_lp_f32(Q, C_, p):
+    """L_p table (delta = |q - c|^p, real p > 0), fp32: C library powf per
+    dim, fp32 adds in dim order."""
+    Q, C_ = _f32(Q), _f32(C_)
+    nq, J = Q.shape
+    M = C_.shape[0]
+    D = np.empty((nq, M, K), np.float32)
+    _ok(lib().bo_lut_lp_f32(Q, nq, J, M, C_, float(p), D), "lut_lp_f32")
+    return D
+
+
+def lut_lp_f64(Q, C_, p):
+    Q, C_ = _f32(Q), _f32(C_)
+    nq, J = Q.shape
+    M = C_.shape[0]
+    D = np.empty((nq, M, K), np.float64)
+    _ok(lib().bo_lut_lp_f64(Q, nq, J, M, C_, float(p), D), "lut_lp_f64")
     return D
 
 

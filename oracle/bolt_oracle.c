@@ -55,8 +55,11 @@
 #define BO_ENOMEM 3
 
 /* L1: delta = |q_j - x_j| (the L_p family of Sec. 1.1 with p = 1; f(r) = r
- * is monotone, so nearest neighbours rank by the sum itself, ascending). */
-enum { BO_METRIC_L2 = 0, BO_METRIC_DOT = 1, BO_METRIC_L1 = 2 };
+ * is monotone, so nearest neighbours rank by the sum itself, ascending).
+ * L_p: delta = |q_j - x_j|^p for a real p > 0 (the same family; f(r) =
+ * r^(1/p) is monotone, so the ranking is again by the sum, ascending); its
+ * tables come from bo_lut_lp_f32 / bo_lut_lp_f64. */
+enum { BO_METRIC_L2 = 0, BO_METRIC_DOT = 1, BO_METRIC_L1 = 2, BO_METRIC_LP = 3 };
 
 /* Largest codebook count; uint16 sums (bo_scan, bo_topk) hold M <= 256. */
 #define BO_MAX_M 4096
@@ -274,6 +277,46 @@ int bo_lut_f64(const float *Q, int64_t nq, int32_t J, int32_t M, const float *C,
     return BO_OK;
 }
 
+/* L_p tables (Sec. 1.1 family, delta = |q_j - c_j|^p, real p > 0): the
+ * entries summed over the subspace's dims in order from the first, each
+ * |q_j - c_j|^p from the C library's powf with fp32 adds; the fp64 form
+ * (pow, fp64 adds) is the reference for the float tolerance.  A GPU's
+ * powf may differ from this one in the last bits, so its tables are
+ * compared within a tolerance and its bytes by quantizing its own floats. */
+int bo_lut_lp_f32(const float *Q, int64_t nq, int32_t J, int32_t M, const float *C, float p, float *D) {
+    int rc = check_shape(nq, J, M);
+    if (rc) return rc;
+    if (!(p > 0.0f) || !(p < INFINITY)) return BO_EINVAL;
+    const int s = J / M;
+    for (int64_t q = 0; q < nq; q++)
+        for (int m = 0; m < M; m++)
+            for (int k = 0; k < BO_K; k++) {
+                const float *c = C + ((int64_t)m * BO_K + k) * s;
+                const float *x = Q + q * J + m * s;
+                float acc = 0.0f;
+                for (int j = 0; j < s; j++) acc = acc + powf(fabsf(x[j] - c[j]), p);
+                D[(q * M + m) * BO_K + k] = acc;
+            }
+    return BO_OK;
+}
+
+int bo_lut_lp_f64(const float *Q, int64_t nq, int32_t J, int32_t M, const float *C, float p, double *D) {
+    int rc = check_shape(nq, J, M);
+    if (rc) return rc;
+    if (!(p > 0.0f) || !(p < INFINITY)) return BO_EINVAL;
+    const int s = J / M;
+    for (int64_t q = 0; q < nq; q++)
+        for (int m = 0; m < M; m++)
+            for (int k = 0; k < BO_K; k++) {
+                const float *c = C + ((int64_t)m * BO_K + k) * s;
+                const float *x = Q + q * J + m * s;
+                double acc = 0.0;
+                for (int j = 0; j < s; j++) acc = acc + pow(fabs((double)x[j] - (double)c[j]), (double)p);
+                D[(q * M + m) * BO_K + k] = acc;
+            }
+    return BO_OK;
+}
+
 /* ---------------------------------------------------------------- beta_m
  * Sec. 3.2: beta_m(y) = max(0, min(255, floor(a (y - b_m)))). */
 static uint8_t quantize_one(float y, float a, float b) {
@@ -462,7 +505,8 @@ static int better(int32_t metric, uint16_t s1, int64_t i1, uint16_t s2, int64_t 
 int bo_topk(const uint16_t *sums, int64_t n, int64_t nq, int32_t k, int32_t metric,
             uint16_t *out_sums, int64_t *out_idx) {
     if (n < 0 || nq < 0 || k <= 0) return BO_EINVAL;
-    if (metric != BO_METRIC_L2 && metric != BO_METRIC_DOT && metric != BO_METRIC_L1) return BO_EINVAL;
+    if (metric != BO_METRIC_L2 && metric != BO_METRIC_DOT && metric != BO_METRIC_L1 && metric != BO_METRIC_LP)
+        return BO_EINVAL;
     for (int64_t q = 0; q < nq; q++) {
         uint16_t *bs = out_sums + q * k;
         int64_t *bi = out_idx + q * k;
@@ -499,7 +543,8 @@ static int better_u32(int32_t metric, uint32_t s1, int64_t i1, uint32_t s2, int6
 int bo_topk_u32(const uint32_t *sums, int64_t n, int64_t nq, int32_t k, int32_t metric,
                 uint32_t *out_sums, int64_t *out_idx) {
     if (n < 0 || nq < 0 || k <= 0) return BO_EINVAL;
-    if (metric != BO_METRIC_L2 && metric != BO_METRIC_DOT && metric != BO_METRIC_L1) return BO_EINVAL;
+    if (metric != BO_METRIC_L2 && metric != BO_METRIC_DOT && metric != BO_METRIC_L1 && metric != BO_METRIC_LP)
+        return BO_EINVAL;
     for (int64_t q = 0; q < nq; q++) {
         uint32_t *bs = out_sums + q * k;
         int64_t *bi = out_idx + q * k;

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbolt.so")
 
 OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, ETIMEOUT = range(6)
-METRIC_L2, METRIC_DOT, METRIC_L1 = 0, 1, 2
+METRIC_L2, METRIC_DOT, METRIC_L1, METRIC_LP = 0, 1, 2, 3
 PREC_FP32, PREC_BF16_RECHECK = 0, 1
 K = 16
 BLOCK = 256
@@ -47,6 +47,8 @@ _SIGS = {
                      C.c_void_p], C.c_int),
     "bolt_build_luts": ([C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_float,
                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_build_luts_lp": ([C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_float, C.c_float,
+                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_scan_l2": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_scan_dot": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_scan_u32": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
@@ -65,6 +67,8 @@ _SIGS = {
                             C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_fit_quantizer": ([C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "bolt_fit_quantizer_lp": ([C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_float, C.c_void_p,
+                               C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_topk_merge": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.c_int32,
                          C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "bolt_write_codes": ([C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
@@ -82,7 +86,7 @@ class Collection(C.Structure):
 
     _fields_ = [("codes", C.c_void_p), ("luts", C.c_void_p), ("sums", C.c_void_p), ("n", C.c_int64),
                 ("nq", C.c_int64), ("ld", C.c_int64), ("M", C.c_int32), ("qt_max", C.c_int32),
-                ("units_per_warp", C.c_int32), ("reserved", C.c_int32)]
+                ("units_per_warp", C.c_int32), ("sum_bits", C.c_int32)]
 
 
 def lib():
@@ -199,6 +203,23 @@ def build_luts(Q, centroids, metric, a, b, out=None, out_f32=False, stream=None)
     bh, bp = _host_f32(b)
     _check(lib().bolt_build_luts(_ptr(Q), nq, J, M, _ptr(centroids), metric, float(a), bp, _ptr(out), _ptr(f32),
                                  _stream(stream)))
+    return (out, f32) if out_f32 else out
+
+
+def build_luts_lp(Q, centroids, p, a, b, out=None, out_f32=False, stream=None):
+    """L_p tables (delta = |q - c|^p, real p > 0): uint8 (nq, M, 16) [and
+    fp32 tables if out_f32]; rank their sums with METRIC_LP."""
+    torch = _torch()
+    _dev(Q, torch.float32, "Q")
+    _dev(centroids, torch.float32, "centroids")
+    nq, J = Q.shape
+    M = centroids.shape[0]
+    if out is None:
+        out = torch.empty((nq, M, K), dtype=torch.uint8, device=Q.device)
+    f32 = torch.empty((nq, M, K), dtype=torch.float32, device=Q.device) if out_f32 else None
+    bh, bp = _host_f32(b)
+    _check(lib().bolt_build_luts_lp(_ptr(Q), nq, J, M, _ptr(centroids), float(p), float(a), bp, _ptr(out),
+                                    _ptr(f32), _stream(stream)))
     return (out, f32) if out_f32 else out
 
 
@@ -463,6 +484,21 @@ def fit_quantizer(Qtrain, centroids, metric, stream=None):
     return np.float32(a.value), b, int(ai.value)
 
 
+def fit_quantizer_lp(Qtrain, centroids, p, stream=None):
+    """The quantizer fit over L_p tables: (a, b[M], alpha_index)."""
+    torch = _torch()
+    _dev(Qtrain, torch.float32, "Qtrain")
+    _dev(centroids, torch.float32, "centroids")
+    nqt, J = Qtrain.shape
+    M = centroids.shape[0]
+    a = C.c_float(0.0)
+    b = np.zeros(M, np.float32)
+    ai = C.c_int32(0)
+    _check(lib().bolt_fit_quantizer_lp(_ptr(Qtrain), nqt, J, M, _ptr(centroids), float(p), C.byref(a),
+                                       b.ctypes.data_as(C.c_void_p), C.byref(ai), _stream(stream)))
+    return np.float32(a.value), b, int(ai.value)
+
+
 # ------------------------------------------------------------------ batched scan
 def sums_ld(n):
     """Row stride (uint16 entries) of a batched-scan sums matrix: n rounded up to 8."""
@@ -474,8 +510,9 @@ class BatchPlan:
 
     ``entries`` is a list of (codes, n, M, luts, sums) with torch CUDA
     tensors: codes blocked, luts (nq, M, 16) uint8, sums (nq, sums_ld(n))
-    uint16.  The plan keeps references to the tensors so their memory stays
-    alive while the plan exists.
+    uint16, or int32 holding the uint32 sums (required for M > 256, up to
+    4096 codebooks).  The plan keeps references to the tensors so their
+    memory stays alive while the plan exists.
     """
 
     def __init__(self, entries, tuning=None, stream=None):
@@ -485,10 +522,12 @@ class BatchPlan:
         for i, (codes, n, M, luts, sums) in enumerate(entries):
             _dev(codes, torch.uint8, "codes")
             _dev(luts, torch.uint8, "luts")
-            _dev(sums, torch.uint16, "sums")
+            wide = sums.dtype == torch.int32
+            _dev(sums, torch.int32 if wide else torch.uint16, "sums")
             nq = luts.shape[0]
             ld = sums.shape[1] if sums.dim() == 2 else sums_ld(n)
-            arr[i] = Collection(codes.data_ptr(), luts.data_ptr(), sums.data_ptr(), n, nq, ld, M, 0, 0, 0)
+            arr[i] = Collection(codes.data_ptr(), luts.data_ptr(), sums.data_ptr(), n, nq, ld, M, 0, 0,
+                                32 if wide else 0)
             if tuning is not None:
                 arr[i].qt_max, arr[i].units_per_warp = tuning[i]
             self._keep += [codes, luts, sums]

@@ -8,9 +8,12 @@
 // warps take the units round-robin.  A warp scans one 256-vector block for
 // qt queries at once: every code word is loaded and prepared once and looked
 // up qt times, with qt sets of accumulators in registers, so the load and
-// the selector preparation are shared by the tile's queries.
+// the selector preparation are shared by the tile's queries.  Collections
+// with uint32 sums (any M up to 4096) sum their codebooks in groups of 256,
+// each group exact in the 16-bit lanes of the lookup core, into 32-bit sums.
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -23,20 +26,23 @@ constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchLutEntries = 1024;  // uint4 table rows staged per task (16 KB)
 
 struct BatchHeader {
-    unsigned int counter;  // next task (reset before every launch)
+    unsigned int counter;       // next uint16-sum task (both counters reset before every run)
+    unsigned int counter_wide;  // next uint32-sum task
     int32_t ntasks;
     int32_t ncoll;
-    int32_t reserved;
     int64_t colls_off;  // byte offsets from the plan base
     int64_t tasks_off;
-    int64_t pad[4];
+    int64_t tasks_wide_off;
+    int32_t ntasks_wide;
+    int32_t reserved;
+    int64_t pad[2];
 };
 static_assert(sizeof(BatchHeader) == 64, "header size");
 
 struct BatchColl {
     const uint32_t *codes;
     const uint4 *luts;
-    uint16_t *sums;
+    uint16_t *sums;  // uint32_t * for collections with uint32 sums (their own task list)
     int64_t n;
     int64_t ld;
     int32_t M;
@@ -51,7 +57,7 @@ struct BatchTask {
     int32_t nb;   // code blocks
     int16_t qt;   // queries per tile (1, 2, 4, 8, 16)
     int16_t nqt;  // tiles in the group
-    int32_t pad;
+    int32_t global_luts;  // 1: the group's tables are read from global memory (too large to stage)
 };
 static_assert(sizeof(BatchTask) == 24, "task size");
 
@@ -89,6 +95,55 @@ __device__ __forceinline__ void batch_unit(const uint32_t *__restrict__ codes, i
             uint32_t e_lo, o_lo, e_hi, o_hi;
             acc[t].finish(e_lo, o_lo, e_hi, o_hi);
             __stcs(reinterpret_cast<uint4 *>(sums + t * ld + v0), pack_sums(e_lo, o_lo, e_hi, o_hi));
+        }
+    }
+}
+
+// The same for uint32 sums: codebooks in groups of 256 (each group's sums
+// exact in the 16-bit lanes), added into 32-bit sums.  lut may point to
+// shared or global memory.
+template <int QT>
+__device__ __forceinline__ void batch_unit_u32(const uint32_t *__restrict__ codes, int64_t b, int M, const uint4 *lut,
+                                               uint32_t *__restrict__ sums, int64_t ld, int64_t n, int lane) {
+    uint32_t tot[QT][8];
+#pragma unroll
+    for (int t = 0; t < QT; ++t)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) tot[t][i] = 0u;
+    const uint32_t *row = codes + b * M * kRowWords + lane;
+    for (int m0 = 0; m0 < M; m0 += 256) {
+        const int m1 = min(M, m0 + 256);
+        Acc8 acc[QT];
+#pragma unroll
+        for (int t = 0; t < QT; ++t) acc[t].zero();
+#pragma unroll 4
+        for (int m = m0; m < m1; ++m) {
+            const WordSel ws = prep_word(__ldg(row + (int64_t)m * kRowWords));
+#pragma unroll
+            for (int t = 0; t < QT; ++t) acc[t].add(ws, lut[t * M + m]);
+        }
+#pragma unroll
+        for (int t = 0; t < QT; ++t) {
+            // e = S0 | S2 << 16, o = S1 | S3 << 16 (vectors 0..3), hi: 4..7
+            uint32_t e_lo, o_lo, e_hi, o_hi;
+            acc[t].finish(e_lo, o_lo, e_hi, o_hi);
+            tot[t][0] += e_lo & 0xFFFFu;
+            tot[t][1] += o_lo & 0xFFFFu;
+            tot[t][2] += e_lo >> 16;
+            tot[t][3] += o_lo >> 16;
+            tot[t][4] += e_hi & 0xFFFFu;
+            tot[t][5] += o_hi & 0xFFFFu;
+            tot[t][6] += e_hi >> 16;
+            tot[t][7] += o_hi >> 16;
+        }
+    }
+    const int64_t v0 = b * kBlockVecs + 8 * lane;
+    if (v0 < n) {  // ld >= n rounded up to 8: the two 16-byte stores stay in the row
+#pragma unroll
+        for (int t = 0; t < QT; ++t) {
+            uint4 *dst = reinterpret_cast<uint4 *>(sums + t * ld + v0);
+            __stcs(dst, make_uint4(tot[t][0], tot[t][1], tot[t][2], tot[t][3]));
+            __stcs(dst + 1, make_uint4(tot[t][4], tot[t][5], tot[t][6], tot[t][7]));
         }
     }
 }
@@ -131,17 +186,58 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_scan_kernel(const uint
     }
 }
 
+// The uint32-sum tasks (collections with sum_bits = 32) in a persistent
+// kernel of their own, so that the uint16 kernel's registers stay as they
+// are; tables are staged in shared memory, or read from global memory when
+// the task's tables are too large to stage.
+__global__ void __launch_bounds__(kBatchThreads, 2) batch_scan_u32_kernel(const uint8_t *__restrict__ plan) {
+    __shared__ uint4 s_lut[kBatchLutEntries];
+    __shared__ int s_task;
+    BatchHeader *hdr = reinterpret_cast<BatchHeader *>(const_cast<uint8_t *>(plan));
+    const int ntasks = hdr->ntasks_wide;
+    const BatchColl *colls = reinterpret_cast<const BatchColl *>(plan + hdr->colls_off);
+    const BatchTask *tasks = reinterpret_cast<const BatchTask *>(plan + hdr->tasks_wide_off);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (;;) {
+        if (tid == 0) s_task = (int)atomicAdd(&hdr->counter_wide, 1u);
+        __syncthreads();
+        const int ti = s_task;
+        if (ti >= ntasks) break;
+        const BatchTask t = tasks[ti];
+        const BatchColl c = colls[t.coll];
+        const int M = c.M;
+        const uint4 *src = c.luts + (int64_t)t.q0 * M;
+        if (!t.global_luts)
+            for (int i = tid; i < (int)t.qt * t.nqt * M; i += kBatchThreads) s_lut[i] = __ldg(src + i);
+        __syncthreads();
+        const uint4 *tab = t.global_luts ? src : s_lut;
+        const int units = t.nb * t.nqt;
+        for (int u = warp; u < units; u += kBatchWarps) {
+            const int tile = u % t.nqt;
+            const int64_t b = (int64_t)t.b0 + u / t.nqt;
+            const uint4 *lut = tab + tile * t.qt * M;
+            uint32_t *dst = reinterpret_cast<uint32_t *>(c.sums) + ((int64_t)t.q0 + (int64_t)tile * t.qt) * c.ld;
+            if (t.qt == 2) batch_unit_u32<2>(c.codes, b, M, lut, dst, c.ld, c.n, lane);
+            else batch_unit_u32<1>(c.codes, b, M, lut, dst, c.ld, c.n, lane);
+        }
+        __syncthreads();  // tables and s_task are reused by the next task
+    }
+}
+
 // ------------------------------------------------------------------ host planning
 static int check_collection(const bolt_collection &c, int i) {
     BOLT_REQUIRE(c.n >= 0 && c.nq >= 0, BOLT_EINVAL, "collection %d: n=%lld nq=%lld", i, (long long)c.n,
                  (long long)c.nq);
-    BOLT_REQUIRE(c.M >= 1 && c.M <= 256, BOLT_EINVAL, "collection %d: M=%d outside [1, 256]", i, c.M);
+    BOLT_REQUIRE(c.sum_bits == 0 || c.sum_bits == 16 || c.sum_bits == 32, BOLT_EINVAL,
+                 "collection %d: sum_bits=%d not in {0, 16, 32}", i, c.sum_bits);
+    const int mmax = c.sum_bits == 32 ? kMaxWideM : 256;
+    BOLT_REQUIRE(c.M >= 1 && c.M <= mmax, BOLT_EINVAL, "collection %d: M=%d outside [1, %d] for %s sums", i, c.M,
+                 mmax, c.sum_bits == 32 ? "uint32" : "uint16");
     BOLT_REQUIRE(c.qt_max == 0 || c.qt_max == 1 || c.qt_max == 2 || c.qt_max == 4 || c.qt_max == 8 ||
                      c.qt_max == 16,
                  BOLT_EINVAL, "collection %d: qt_max=%d not in {0,1,2,4,8,16}", i, c.qt_max);
     BOLT_REQUIRE(c.units_per_warp >= 0 && c.units_per_warp <= 64, BOLT_EINVAL,
                  "collection %d: units_per_warp=%d outside [0, 64]", i, c.units_per_warp);
-    BOLT_REQUIRE(c.reserved == 0, BOLT_EINVAL, "collection %d: reserved field must be 0", i);
     BOLT_REQUIRE(num_blocks(c.n) < (int64_t)1 << 31 && c.nq < (int64_t)1 << 31, BOLT_EINVAL,
                  "collection %d too large", i);
     if (c.n == 0 || c.nq == 0) return BOLT_OK;
@@ -156,8 +252,13 @@ static int check_collection(const bolt_collection &c, int i) {
 static void plan_collection(const bolt_collection &c, int32_t ci, std::vector<BatchTask> &out) {
     if (c.n == 0 || c.nq == 0) return;
     const int M = c.M;
+    const bool wide = c.sum_bits == 32;
     int qmax = c.qt_max ? c.qt_max : 8;
-    while (qmax > 1 && qmax * M > kBatchLutEntries) qmax >>= 1;
+    if (wide && qmax > 2) qmax = 2;  // 8 uint32 totals per query in registers
+    // tiles shrink until their tables can be staged (tables of more than
+    // kBatchLutEntries rows are read from global memory at any tile size)
+    if (M <= kBatchLutEntries)
+        while (qmax > 1 && qmax * M > kBatchLutEntries) qmax >>= 1;
     const int upw = c.units_per_warp ? c.units_per_warp : 4;
     const int64_t nbt = num_blocks(c.n);
     // query tiles: qmax-sized, the remainder split into powers of two
@@ -187,7 +288,7 @@ static void plan_collection(const bolt_collection &c, int32_t ci, std::vector<Ba
             t.nb = (int32_t)std::min<int64_t>(nb, nbt - b0);
             t.qt = (int16_t)g.qt;
             t.nqt = (int16_t)g.nqt;
-            t.pad = 0;
+            t.global_luts = g.qt * g.nqt * M > kBatchLutEntries ? 1 : 0;
             mine.push_back(t);
         }
     }
@@ -211,18 +312,20 @@ static int build_plan_host(const bolt_collection *colls, int32_t ncoll, std::vec
         const double wb = (double)colls[b].n * (double)colls[b].nq * colls[b].M;
         return wa > wb;
     });
-    std::vector<BatchTask> tasks;
-    for (int i : order) plan_collection(colls[i], i, tasks);
-    BOLT_REQUIRE(tasks.size() < (size_t)1 << 31, BOLT_EINVAL, "too many tasks");
+    std::vector<BatchTask> tasks, tasks_wide;
+    for (int i : order) plan_collection(colls[i], i, colls[i].sum_bits == 32 ? tasks_wide : tasks);
+    BOLT_REQUIRE(tasks.size() + tasks_wide.size() < (size_t)1 << 31, BOLT_EINVAL, "too many tasks");
     const int64_t colls_off = sizeof(BatchHeader);
     const int64_t tasks_off = colls_off + (int64_t)ncoll * (int64_t)sizeof(BatchColl);
-    blob.assign((size_t)(tasks_off + (int64_t)tasks.size() * (int64_t)sizeof(BatchTask)), 0);
+    const int64_t tasks_wide_off = tasks_off + (int64_t)tasks.size() * (int64_t)sizeof(BatchTask);
+    blob.assign((size_t)(tasks_wide_off + (int64_t)tasks_wide.size() * (int64_t)sizeof(BatchTask)), 0);
     BatchHeader h{};
-    h.counter = 0;
     h.ntasks = (int32_t)tasks.size();
     h.ncoll = ncoll;
     h.colls_off = colls_off;
     h.tasks_off = tasks_off;
+    h.tasks_wide_off = tasks_wide_off;
+    h.ntasks_wide = (int32_t)tasks_wide.size();
     memcpy(blob.data(), &h, sizeof(h));
     for (int i = 0; i < ncoll; ++i) {
         BatchColl r{};
@@ -235,6 +338,8 @@ static int build_plan_host(const bolt_collection *colls, int32_t ncoll, std::vec
         memcpy(blob.data() + colls_off + (int64_t)i * sizeof(BatchColl), &r, sizeof(r));
     }
     if (!tasks.empty()) memcpy(blob.data() + tasks_off, tasks.data(), tasks.size() * sizeof(BatchTask));
+    if (!tasks_wide.empty())
+        memcpy(blob.data() + tasks_wide_off, tasks_wide.data(), tasks_wide.size() * sizeof(BatchTask));
     return BOLT_OK;
 }
 
@@ -254,13 +359,28 @@ static int batch_grid(int *grid) {
     return BOLT_OK;
 }
 
+// Plans with uint32-sum tasks, recorded when a plan is uploaded (a plan not
+// recorded here, e.g. one copied by the caller, runs both kernels: the wide
+// one then finds no tasks).
+static std::mutex g_plans_mu;
+static std::map<const void *, bool> g_plan_wide;
+
 static int run_plan(const void *plan, cudaStream_t s) {
     int grid = 0;
     int rc = batch_grid(&grid);
     if (rc) return rc;
-    BOLT_CUDA(cudaMemsetAsync(const_cast<void *>(plan), 0, sizeof(unsigned int), s));
+    bool wide = true;
+    {
+        std::lock_guard<std::mutex> lk(g_plans_mu);
+        auto it = g_plan_wide.find(plan);
+        if (it != g_plan_wide.end()) wide = it->second;
+    }
+    BOLT_CUDA(cudaMemsetAsync(const_cast<void *>(plan), 0, 2 * sizeof(unsigned int), s));
     batch_scan_kernel<<<grid, kBatchThreads, 0, s>>>(reinterpret_cast<const uint8_t *>(plan));
-    return check_launch("batch_scan_kernel");
+    rc = check_launch("batch_scan_kernel");
+    if (rc || !wide) return rc;
+    batch_scan_u32_kernel<<<grid, kBatchThreads, 0, s>>>(reinterpret_cast<const uint8_t *>(plan));
+    return check_launch("batch_scan_u32_kernel");
 }
 
 static int upload_plan(const std::vector<uint8_t> &blob, void *plan, int64_t plan_bytes, cudaStream_t s) {
@@ -270,6 +390,10 @@ static int upload_plan(const std::vector<uint8_t> &blob, void *plan, int64_t pla
                  (long long)plan_bytes, (long long)blob.size());
     BOLT_CUDA(cudaMemcpyAsync(plan, blob.data(), blob.size(), cudaMemcpyHostToDevice, s));
     BOLT_CUDA(cudaStreamSynchronize(s));
+    BatchHeader h;
+    memcpy(&h, blob.data(), sizeof(h));
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    g_plan_wide[plan] = h.ntasks_wide > 0;
     return BOLT_OK;
 }
 
@@ -336,6 +460,10 @@ int bolt_batch_autotune(bolt_collection *colls_host, int32_t ncoll, void *stream
     auto cleanup = [&]() {
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
+        {
+            std::lock_guard<std::mutex> lk(bolt::g_plans_mu);
+            bolt::g_plan_wide.erase(plan);
+        }
         cudaFree(plan);
     };
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {

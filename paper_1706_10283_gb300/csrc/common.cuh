@@ -62,6 +62,13 @@ constexpr int kMaxWideM = 4096;
 int check_nm_wide(int64_t n, int32_t M);
 int check_jm_wide(int32_t J, int32_t M);
 
+// Metrics whose sums the top-k family ranks (L2, L1 and L_p ascending, dot
+// descending).
+__host__ __device__ inline bool rank_metric_ok(int32_t metric) {
+    return metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT || metric == BOLT_METRIC_L1 ||
+           metric == BOLT_METRIC_LP;
+}
+
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -194,7 +194,8 @@ struct DevBuf {
 };
 
 static int fit_quantizer_impl(const float *Qtrain, int64_t nqt, int32_t J, int32_t M, const float *C, int32_t metric,
-                              float *a_host, float *b_host, int32_t *alpha_idx_host, cudaStream_t s) {
+                              float *a_host, float *b_host, int32_t *alpha_idx_host, cudaStream_t s,
+                              float p = 1.0f) {
     DevBuf dD, dOut;
     const size_t nD = (size_t)nqt * M * kK;
     BOLT_CUDA(cudaMalloc(&dD.p, nD * (sizeof(float) + 1)));
@@ -204,7 +205,7 @@ static int fit_quantizer_impl(const float *Qtrain, int64_t nqt, int32_t J, int32
     QuantParams qp;
     qp.a = 1.0f;
     for (int m = 0; m < 256; ++m) qp.b[m] = 0.0f;
-    int rc = launch_build_luts(Qtrain, nqt, J, M, C, metric, qp, scratch_luts, D, s);
+    int rc = launch_build_luts(Qtrain, nqt, J, M, C, metric, qp, scratch_luts, D, s, nullptr, p);
     if (rc) return rc;
     double *out_a = static_cast<double *>(dOut.p);
     double *out_loss = out_a + 8;
@@ -273,6 +274,18 @@ int bolt_fit_quantizer(const float *Qtrain, int64_t nqt, int32_t J, int32_t M, c
     BOLT_REQUIRE(Qtrain && centroids && a_host && b_host, BOLT_EINVAL, "null pointer");
     return bolt::fit_quantizer_impl(Qtrain, nqt, J, M, centroids, metric, a_host, b_host, alpha_idx_host,
                                     (cudaStream_t)stream);
+}
+
+int bolt_fit_quantizer_lp(const float *Qtrain, int64_t nqt, int32_t J, int32_t M, const float *centroids, float p,
+                          float *a_host, float *b_host, int32_t *alpha_idx_host, void *stream) {
+    bolt::clear_error();
+    int rc = bolt::check_jm(J, M);
+    if (rc) return rc;
+    BOLT_REQUIRE(nqt >= 1, BOLT_EINVAL, "need at least one training query");
+    BOLT_REQUIRE(p > 0.0f && p < INFINITY, BOLT_EINVAL, "exponent p=%g must be positive and finite", (double)p);
+    BOLT_REQUIRE(Qtrain && centroids && a_host && b_host, BOLT_EINVAL, "null pointer");
+    return bolt::fit_quantizer_impl(Qtrain, nqt, J, M, centroids, BOLT_METRIC_LP, a_host, b_host, alpha_idx_host,
+                                    (cudaStream_t)stream, p);
 }
 
 int bolt_fit_codebooks(const float *X, int64_t n, int32_t J, int32_t M, int32_t iters, const int64_t *init_rows_host,

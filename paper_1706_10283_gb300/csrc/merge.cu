@@ -104,7 +104,7 @@ extern "C" int bolt_topk_merge(const uint16_t *sums, const int64_t *idx, const i
     BOLT_REQUIRE(nq >= 0 && nq <= 0x7FFFFFFF, BOLT_EINVAL, "nq=%lld", (long long)nq);
     BOLT_REQUIRE(k >= 1 && k <= 1024, BOLT_EUNSUPPORTED, "k=%d outside [1, 1024]", k);
     BOLT_REQUIRE(M >= 1 && M <= 256, BOLT_EUNSUPPORTED, "M=%d outside [1, 256]", M);
-    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT || metric == BOLT_METRIC_L1, BOLT_EINVAL,
+    BOLT_REQUIRE(bolt::rank_metric_ok(metric), BOLT_EINVAL,
                  "bad metric %d", metric);
     if (nq == 0) return BOLT_OK;
     BOLT_REQUIRE(sums && idx && offsets && out_sums && out_idx, BOLT_EINVAL, "null pointer");

@@ -1151,7 +1151,7 @@ int bolt_topk(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, i
     int rc = bolt::check_nm(n, M);
     if (rc) return rc;
     BOLT_REQUIRE(nq >= 0, BOLT_EINVAL, "nq=%lld < 0", (long long)nq);
-    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT || metric == BOLT_METRIC_L1, BOLT_EINVAL,
+    BOLT_REQUIRE(bolt::rank_metric_ok(metric), BOLT_EINVAL,
                  "bad metric %d", metric);
     bolt::TopkPlan plan;
     rc = bolt::plan_topk(n, M, k, nq, &plan);
@@ -1220,7 +1220,7 @@ extern "C" int bolt_topk_noalloc(const uint8_t *codes, int64_t n, int32_t M, con
     int rc = bolt::check_nm(n, M);
     if (rc) return rc;
     BOLT_REQUIRE(nq >= 0, BOLT_EINVAL, "nq=%lld < 0", (long long)nq);
-    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT || metric == BOLT_METRIC_L1, BOLT_EINVAL,
+    BOLT_REQUIRE(bolt::rank_metric_ok(metric), BOLT_EINVAL,
                  "bad metric %d", metric);
     bolt::TopkPlan plan;
     rc = bolt::plan_topk(n, M, k, nq, &plan);

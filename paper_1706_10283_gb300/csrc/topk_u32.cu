@@ -64,7 +64,6 @@ static U32WS carve_u32(void *ws, int64_t n, int64_t nq, int32_t k) {
     U32WS w;
     w.sums = reinterpret_cast<uint32_t *>(p);
     p += u32_align((size_t)nq * n * 4);
-    uint8_t *hdr = p;
     w.hi = reinterpret_cast<uint32_t *>(p);
     w.lo = w.hi + (size_t)nq * kU32Hi;
     p += u32_align((size_t)nq * (kU32Hi + kU32Lo) * 4);
@@ -72,7 +71,6 @@ static U32WS carve_u32(void *ws, int64_t n, int64_t nq, int32_t k) {
     p += u32_align((size_t)nq * G * 4);
     w.nlt = reinterpret_cast<uint32_t *>(p);
     p += u32_align((size_t)nq * 4);
-    (void)hdr;
     w.cand = reinterpret_cast<uint64_t *>(p);
     (void)k;
     return w;
@@ -303,7 +301,7 @@ int bolt_topk_u32(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *lut
     if (rc) return rc;
     BOLT_REQUIRE(nq >= 0, BOLT_EINVAL, "nq=%lld < 0", (long long)nq);
     BOLT_REQUIRE(k >= 1 && k <= bolt::kU32MaxK, BOLT_EUNSUPPORTED, "k=%d outside [1, %d]", k, bolt::kU32MaxK);
-    BOLT_REQUIRE(metric == BOLT_METRIC_L2 || metric == BOLT_METRIC_DOT || metric == BOLT_METRIC_L1, BOLT_EINVAL,
+    BOLT_REQUIRE(bolt::rank_metric_ok(metric), BOLT_EINVAL,
                  "bad metric %d", metric);
     BOLT_REQUIRE(n < (int64_t)1 << 31, BOLT_EUNSUPPORTED, "n=%lld: indices must fit 31 bits", (long long)n);
     BOLT_REQUIRE(nq <= 65535, BOLT_EUNSUPPORTED, "nq=%lld > 65535 per call", (long long)nq);

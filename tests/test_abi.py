@@ -89,8 +89,8 @@ def test_binding_fails_loudly_without_cuda():
         bolt.encode(torch.zeros(4, 8), torch.zeros(2, 16, 4))
 
 
-def _coll(n, M, nq, ld=None, qt=0, upw=0, codes=0x10000, luts=0x20000, sums=0x30000, reserved=0):
-    return bolt.Collection(codes, luts, sums, n, nq, bolt.sums_ld(n) if ld is None else ld, M, qt, upw, reserved)
+def _coll(n, M, nq, ld=None, qt=0, upw=0, codes=0x10000, luts=0x20000, sums=0x30000, sum_bits=0):
+    return bolt.Collection(codes, luts, sums, n, nq, bolt.sums_ld(n) if ld is None else ld, M, qt, upw, sum_bits)
 
 
 def _plan_bytes(*colls):
@@ -113,12 +113,21 @@ def test_batch_planner_task_counts():
     assert _plan_bytes(_coll(256, 256, 9, qt=16, upw=1)) == H + R + 3 * T
     # empty collections have no tasks but keep their record
     assert _plan_bytes(_coll(0, 8, 5), _coll(100, 8, 0)) == H + 2 * R
+    # uint32 sums: at most 2 queries per tile; M = 300 stages one query's
+    # 300 table rows per group (5 queries -> tiles 2, 2, 1, one per group);
+    # M = 2048 (too large to stage) also tiles of 2
+    assert _plan_bytes(_coll(256, 300, 5, qt=16, upw=1, sum_bits=32)) == H + R + 3 * T
+    assert _plan_bytes(_coll(256, 2048, 4, qt=8, upw=1, sum_bits=32)) == H + R + 2 * T
+    # both lists in one plan: the uint16 tasks, then the uint32 ones
+    assert _plan_bytes(_coll(100, 16, 37, qt=8, upw=4), _coll(256, 300, 5, qt=16, upw=1, sum_bits=32)) == \
+        H + 2 * R + 6 * T
 
 
 def test_batch_planner_rejects_bad_collections():
     L = bolt.lib()
     bad = [_coll(100, 0, 2), _coll(100, 257, 2), _coll(100, 8, 2, ld=100), _coll(100, 8, 2, ld=96),
-           _coll(100, 8, 2, qt=3), _coll(100, 8, 2, upw=65), _coll(100, 8, 2, reserved=1),
+           _coll(100, 8, 2, qt=3), _coll(100, 8, 2, upw=65), _coll(100, 8, 2, sum_bits=1),
+           _coll(100, 8, 2, sum_bits=8), _coll(100, 4097, 2, sum_bits=32), _coll(100, 257, 2, sum_bits=16),
            _coll(100, 8, 2, codes=0x10001), _coll(100, 8, 2, sums=0), _coll(-1, 8, 2)]
     for c in bad:
         assert _plan_bytes(c) < 0

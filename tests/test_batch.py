@@ -184,6 +184,48 @@ def test_batched_edge_cases(torch_cuda):
         np.testing.assert_array_equal(host[off + nq * ld:off + nq * ld + 8], 0x1234)
 
 
+def test_batched_uint32_sums_large_M(torch_cuda):
+    """Collections with uint32 sums in the same plan as uint16 ones: M above
+    256 (300, 1030: tables staged; 2048: tables read from global memory, too
+    large to stage), ragged n, 1..5 queries, and a uint32 collection with
+    M = 16; every sum against the oracle's uint32 scan.  The uint16
+    collections' results are unchanged by the wide tasks beside them, and a
+    tuned plan gives the same sums."""
+    torch = torch_cuda
+    rng = np.random.default_rng(23)
+    shapes = [(5_003, 300, 3, True), (2_049, 1030, 2, True), (777, 2048, 5, True), (10_007, 16, 4, True),
+              (20_001, 16, 7, False), (3_001, 8, 33, False)]
+    ents, refs, outs = [], [], []
+    for n, M, nq, wide in shapes:
+        codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+        luts = rng.integers(0, 256, (nq, M, 16)).astype(np.uint8)
+        ld = bolt.sums_ld(n)
+        if wide:
+            sums = torch.full((nq, ld), -1, dtype=torch.int32, device="cuda")
+            refs.append(oracle.scan_u32(codes, luts).astype(np.uint32))
+        else:
+            sums = u16(torch, (nq, ld), 0xBEEF)
+            refs.append(oracle.scan(codes, luts))
+        ents.append((bolt.pack_codes(dev(torch, codes)), n, M, dev(torch, luts), sums))
+        outs.append((sums, n, wide))
+
+    def check():
+        for (sums, n, wide), ref in zip(outs, refs):
+            got = sums[:, :n].cpu().numpy()
+            np.testing.assert_array_equal(got.view(np.uint32) if wide else got, ref)
+
+    plan = bolt.BatchPlan(ents)
+    plan.run()
+    torch.cuda.synchronize()
+    check()
+    for sums, n, wide in outs:
+        sums.fill_(0)
+    plan.autotune()
+    plan.run()
+    torch.cuda.synchronize()
+    check()
+
+
 def test_batched_invalid_arguments(torch_cuda):
     torch = torch_cuda
     codes = torch.zeros(bolt.codes_bytes(100, 8), dtype=torch.uint8, device="cuda")
@@ -195,6 +237,10 @@ def test_batched_invalid_arguments(torch_cuda):
         bolt.BatchPlan([(codes, 100, 8, luts, sums)], tuning=[(3, 1)])  # qt_max 3
     with pytest.raises(bolt.BoltError):
         bolt.BatchPlan([(codes[1:], 100, 8, luts, sums)])  # misaligned codes
+    big = torch.zeros(bolt.codes_bytes(100, 300), dtype=torch.uint8, device="cuda")
+    bl = torch.zeros((2, 300, 16), dtype=torch.uint8, device="cuda")
+    with pytest.raises(bolt.BoltError):
+        bolt.BatchPlan([(big, 100, 300, bl, sums)])  # M > 256 needs uint32 sums
 
 
 # ------------------------------------------------------------------ full size

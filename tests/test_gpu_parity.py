@@ -234,6 +234,44 @@ def test_topk_l1_tables_rank_ascending(torch_cuda, n, M, k, nq):
     check_topk(torch_cuda, codes, luts, k, bolt.METRIC_L1)
 
 
+@pytest.mark.parametrize("p", [0.5, 1.5, 3.0])
+def test_lp_tables_fit_and_topk(torch_cuda, p):
+    """L_p tables (delta = |q - c|^p): the GPU's fp32 entries (CUDA powf)
+    within 1e-5 of the oracle's fp64 tables; its bytes equal the oracle's
+    quantization of those fp32 entries; the quantizer fit over L_p tables
+    equals the oracle's fit of the same fp32 tables; and top-k with the L_p
+    metric over the GPU's bytes equals the oracle's, in the shared-memory,
+    streaming and multi-query size classes."""
+    torch = torch_cuda
+    rng = np.random.default_rng(int(p * 10))
+    J, M = 64, 16
+    X = synth.mixture(30_000, J, 71)
+    C_ = oracle.kmeans(X[:5_000], M, 4, synth.kmeans_init_rows(5_000, 71))
+    Qtr = X[synth.train_query_rows(30_000, 71)]
+    Q = synth.mixture(5, J, 72)
+    Cd = dev(torch, C_)
+    # fit: over the GPU's own fp32 tables of the training queries
+    _, Dtr = bolt.build_luts_lp(dev(torch, Qtr), Cd, p, 1.0, np.zeros(M, np.float32), out_f32=True)
+    a, b, ai = bolt.fit_quantizer_lp(dev(torch, Qtr), Cd, p)
+    oa, ob, oai, _ = oracle.fit_quant(Dtr.cpu().numpy())
+    assert (a, ai) == (np.float32(oa), oai)
+    np.testing.assert_array_equal(b, ob)
+    luts, D = bolt.build_luts_lp(dev(torch, Q), Cd, p, a, b, out_f32=True)
+    Dg = D.cpu().numpy()
+    ref = oracle.lut_lp_f64(Q, C_, p)
+    np.testing.assert_allclose(Dg, ref, rtol=1e-5, atol=1e-5 * float(np.abs(ref).max()))
+    lg = luts.cpu().numpy()
+    np.testing.assert_array_equal(lg, oracle.quantize(Dg, a, b))
+    for n in (10_003, 4_000_000):
+        codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+        blocked = bolt.pack_codes(dev(torch, codes))
+        for nq in (1, 5):
+            s_, i_ = bolt.topk(blocked, n, M, luts[:nq], 100, bolt.METRIC_LP)
+            rs, ri = oracle.topk(oracle.scan(codes, lg[:nq]), 100, oracle.METRIC_LP)
+            np.testing.assert_array_equal(i_.cpu().numpy(), ri)
+            np.testing.assert_array_equal(s_.cpu().numpy(), rs)
+
+
 @pytest.mark.parametrize("metric", [bolt.METRIC_L2, bolt.METRIC_DOT])
 def test_topk_heavy_ties(torch_cuda, metric):
     """Tables with 2 distinct values: huge tie groups decided by index."""

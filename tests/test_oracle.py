@@ -580,3 +580,61 @@ def test_parallel_encode_equals_encode():
     X = rng.standard_normal((10_007, 16)).astype(np.float32)
     C = rng.standard_normal((4, 16, 4)).astype(np.float32)
     np.testing.assert_array_equal(parallel.encode(X, C, threads=3, chunk=1000), oracle.encode(X, C))
+
+
+# ------------------------------------------------------------------ L_p tables
+def test_lp_tables_reduce_to_l1_and_l2():
+    """p = 1 is the L1 table (powf(t, 1) = t exactly); p = 2 in fp64 is the
+    L2 table up to the last bit of a term (pow(t, 2) against t * t)."""
+    rng = np.random.default_rng(40)
+    Q = rng.standard_normal((5, 24)).astype(np.float32)
+    C = rng.standard_normal((6, 16, 4)).astype(np.float32)
+    np.testing.assert_array_equal(oracle.lut_lp_f32(Q, C, 1.0), oracle.lut_f32(Q, C, oracle.METRIC_L1))
+    np.testing.assert_allclose(oracle.lut_lp_f64(Q, C, 2.0), oracle.lut_f64(Q, C, oracle.METRIC_L2), rtol=1e-14)
+
+
+def test_lp_tables_closed_forms():
+    """One differing coordinate d gives |d|^p exactly for exact powers
+    (2^3 = 8, 4^0.5 = 2, 0.25^1.5 = 0.125, 3^0 is excluded: p > 0), and a
+    query on a centroid gives 0; the entries of the other centroids follow
+    the subspace's own dims only."""
+    s = 4
+    C = np.zeros((2, 16, s), np.float32)
+    for k in range(16):
+        C[:, k, :] = k  # centroid k of both subspaces: all coordinates k
+    for d, p, want in ((2.0, 3.0, 8.0), (4.0, 0.5, 2.0), (0.25, 1.5, 0.125)):
+        q = np.zeros((1, 2 * s), np.float32)
+        q[0, 1] = d  # subspace 0: one coordinate d away from centroid 0
+        D = oracle.lut_lp_f64(q, C, p)
+        assert D[0, 0, 0] == want
+        assert D[0, 1, 0] == 0.0  # subspace 1: the query is on centroid 0
+        # centroid 5 in subspace 1: four coordinates 5 away
+        assert D[0, 1, 5] == pytest.approx(4 * 5.0 ** p, rel=1e-15)
+        assert oracle.lut_lp_f32(q, C, p)[0, 0, 0] == np.float32(want)
+
+
+@pytest.mark.parametrize("p", [0.5, 1.5, 3.0])
+def test_lp_tables_homogeneous_and_fp32_close(p):
+    """Scaling query and centroids by 2 scales every entry by 2^p (fp64,
+    up to rounding), and the fp32 table is within 1e-5 of the fp64 one."""
+    rng = np.random.default_rng(41)
+    Q = rng.standard_normal((4, 32)).astype(np.float32)
+    C = rng.standard_normal((8, 16, 4)).astype(np.float32)
+    D = oracle.lut_lp_f64(Q, C, p)
+    D2 = oracle.lut_lp_f64(2 * Q, 2 * C, p)
+    np.testing.assert_allclose(D2, D * 2.0 ** p, rtol=1e-12)
+    np.testing.assert_allclose(oracle.lut_lp_f32(Q, C, p), D, rtol=1e-5, atol=1e-6)
+    with pytest.raises(oracle.OracleError):
+        oracle.lut_lp_f32(Q, C, 0.0)
+
+
+def test_lp_metric_ranks_ascending():
+    """Top-k of L_p sums ranks ascending with ties to the lower index, the
+    same order as L1."""
+    rng = np.random.default_rng(42)
+    S = rng.integers(0, 50, (3, 2000)).astype(np.uint16)
+    a = oracle.topk(S, 37, oracle.METRIC_LP)
+    b = oracle.topk(S, 37, oracle.METRIC_L1)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    assert (np.diff(a[0].astype(int), axis=1) >= 0).all()
