@@ -89,6 +89,15 @@ class Collection(C.Structure):
                 ("units_per_warp", C.c_int32), ("sum_bits", C.c_int32)]
 
 
+def _load(path):
+    L = C.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
 def lib():
     """Load libbolt.so (building it first if it is missing or stale)."""
     global _lib
@@ -99,12 +108,18 @@ def lib():
             _build.build()
         if not os.path.exists(LIB_PATH):
             raise BoltError(ECUDA, "libbolt.so is not built")
-        L = C.CDLL(LIB_PATH)
-        for name, (args, res) in _SIGS.items():
-            fn = getattr(L, name)
-            fn.argtypes = args
-            fn.restype = res
-        _lib = L
+        _lib = _load(LIB_PATH)
+    return _lib
+
+
+def load_library(path):
+    """Use the library at `path` (a build of the same sources, e.g. the
+    diagnostic libbolt_stamps.so) instead of libbolt.so in this process;
+    call before any other function of this module."""
+    global _lib
+    if _lib is not None:
+        raise BoltError(EINVAL, "a library is already loaded in this process")
+    _lib = _load(path)
     return _lib
 
 

@@ -3,6 +3,10 @@
 Each ``csrc/*.cu`` translation unit is compiled by nvcc in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo``, then linked into
 ``paper_1706_10283_gb300/libbolt.so`` with the static CUDA runtime.
+
+``build(stamps=True)`` makes the diagnostic variant ``libbolt_stamps.so``
+(``-DBOLT_PHASE_STAMPS``: the top-k kernels record per-CTA phase times,
+read by ``phases.py``); the library itself never contains the stamps.
 """
 import concurrent.futures as cf
 import glob
@@ -15,6 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbolt.so")
+BUILD_STAMPS = os.path.join(HERE, "_build_stamps")
+LIB_STAMPS = os.path.join(HERE, "libbolt_stamps.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -40,23 +46,25 @@ def _deps():
         os.path.join(HERE, "..", "include", "*.h"))
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force=False, verbose=False, jobs=None):
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, jobs=None, stamps=False):
+    lib, bdir = (LIB_STAMPS, BUILD_STAMPS) if stamps else (LIB, BUILD)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     srcs = _sources()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(bdir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    extra = ["-DBOLT_PHASE_STAMPS"] if stamps else []
 
     def compile_one(src_obj):
         src, obj = src_obj
-        cmd = [nvcc()] + _flags(verbose) + ["-c", src, "-o", obj]
+        cmd = [nvcc()] + _flags(verbose) + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         return src, r.returncode, r.stdout + r.stderr
 
@@ -68,14 +76,14 @@ def build(force=False, verbose=False, jobs=None):
             sys.stderr.write("== %s\n%s\n" % (os.path.basename(s), out))
     if failed:
         raise RuntimeError("nvcc failed for: " + ", ".join(os.path.basename(s) for s, _ in failed))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc(), ARCH, "-shared", "-cudart", "static", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, stamps="--stamps" in sys.argv))

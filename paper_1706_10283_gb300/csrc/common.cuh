@@ -69,6 +69,31 @@ __host__ __device__ inline bool rank_metric_ok(int32_t metric) {
            metric == BOLT_METRIC_LP;
 }
 
+// ------------------------------------------------------------------ phase stamps
+// Diagnostic builds only (-DBOLT_PHASE_STAMPS, libbolt_stamps.so; see
+// paper_1706_10283_gb300/phases.py): a kernel's thread 0 of CTA c of query 0
+// records the global timer, or a count, in slot i of its kernel's stamp
+// array.  In the library itself the macros expand to nothing.
+#ifdef BOLT_PHASE_STAMPS
+#define BOLT_STAMP_ARRAY(name) __device__ unsigned long long name[1024 * 16]
+#define BOLT_STAMP(arr, q, cta, i) \
+    do {                                                                         \
+        if ((q) == 0 && (cta) < 1024 && threadIdx.x == 0) arr[(cta) * 16 + (i)] = ::bolt::globaltimer_ns(); \
+    } while (0)
+#define BOLT_STAMP_VALUE(arr, q, cta, i, v) \
+    do {                                                                          \
+        if ((q) == 0 && (cta) < 1024 && threadIdx.x == 0) arr[(cta) * 16 + (i)] = (unsigned long long)(v); \
+    } while (0)
+#else
+#define BOLT_STAMP_ARRAY(name) static_assert(true, "")
+#define BOLT_STAMP(arr, q, cta, i) \
+    do {                           \
+    } while (0)
+#define BOLT_STAMP_VALUE(arr, q, cta, i, v) \
+    do {                                    \
+    } while (0)
+#endif
+
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

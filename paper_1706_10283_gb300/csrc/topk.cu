@@ -57,6 +57,10 @@ namespace bolt {
 // draining copies in flight after a failure (waits for the CTA's own code
 // copies use data_wait_limit_ns(), 1 s by default)
 constexpr uint64_t kWaitLimit = 1000000000ull;
+// phase stamps (diagnostic builds): 0 start, 1 first threshold, 2 loop end,
+// 3 published, 4 end (last CTA), 5 keys published, 6 merge total, 7 merge
+// survivors, 8 last CTA's counts and bound, 9 gathered
+BOLT_STAMP_ARRAY(g_stamps_topk);
 constexpr int kMaxStages = 8;
 constexpr size_t kStageBudget = 128 * 1024;
 constexpr int kMaxK = 1024;
@@ -376,6 +380,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     if (active != nullptr && active[q] == 0u) return;  // only the queries marked for this kernel
     const int G = gridDim.x, cta = blockIdx.x;
     if (MT > 0) M = MT;
+    BOLT_STAMP(g_stamps_topk, q, cta, 0);
     const uint32_t blk_bytes = (uint32_t)M * kRowBytes;
     const uint32_t stage_bytes = BPI * blk_bytes;
 
@@ -687,6 +692,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
                     }
                 }
             seed_barrier(seeders);
+            BOLT_STAMP(g_stamps_topk, q, cta, 1);
             uint32_t cbin, fbin, in_bin, c[8];
             if (warp_kth_bin<false>(chist, hist, (uint32_t)k, lane, cbin, fbin, in_bin, c)) {
                 const uint32_t seed = (fbin + 1u) << hshift;
@@ -826,6 +832,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     }
     __syncthreads();
 
+    BOLT_STAMP(g_stamps_topk, q, cta, 2);
     // Wait (bounded) for copies still in flight after a failure, so that no
     // bulk copy targets this CTA's shared memory after it exits.
     if (failed && lane == 0) {
@@ -856,6 +863,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     }
     __threadfence();
     __syncthreads();
+    BOLT_STAMP(g_stamps_topk, q, cta, 3);
+    BOLT_STAMP_VALUE(g_stamps_topk, q, cta, 5, cnt);
     if (tid == 0) misc[3] = (atomicAdd(&ws.ticket[q], 1u) == (uint32_t)(G - 1)) ? 1u : 0u;
     __syncthreads();
     if (vmisc[3] == 0) return;
@@ -904,6 +913,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     }
     __syncthreads();
     const uint32_t total = vmisc_hist(off, G);
+    BOLT_STAMP(g_stamps_topk, q, cta, 8);
+    BOLT_STAMP_VALUE(g_stamps_topk, q, cta, 6, total);
     const uint32_t bfin = total > (uint32_t)kRankSortMax ? vmisc[5] : 0xFFFFFFFFu;
     uint64_t *mk = reinterpret_cast<uint64_t *>(smem);
     uint32_t kept_all = 0;
@@ -954,6 +965,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         __syncthreads();
     }
     int g = (int)kept_all;
+    BOLT_STAMP(g_stamps_topk, q, cta, 9);
+    BOLT_STAMP_VALUE(g_stamps_topk, q, cta, 7, g);
     const bool bad = vmisc[2] != 0u;
     auto emit = [&](int r, uint64_t key) {
         const uint32_t sp = (uint32_t)(key >> 32);
@@ -990,6 +1003,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         out_sums[q * k + r] = 0;
         out_idx[q * k + r] = bad ? -2 : -1;
     }
+    BOLT_STAMP(g_stamps_topk, q, cta, 4);
 }
 
 // ------------------------------------------------------------------ host side
@@ -1133,6 +1147,20 @@ int launch_topk_stream(const uint8_t *codes, int64_t n, int32_t M, const uint8_t
 }
 
 }  // namespace bolt
+
+#ifdef BOLT_PHASE_STAMPS
+// Copies the streaming kernel's stamps (1024 CTAs x 16 slots) to host and,
+// with clear != 0, zeroes them (diagnostic builds only).
+extern "C" int bolt_debug_stamps_topk(unsigned long long *host, int clear) {
+    if (cudaMemcpyFromSymbol(host, bolt::g_stamps_topk, sizeof(unsigned long long) * 1024 * 16) != cudaSuccess)
+        return BOLT_ECUDA;
+    if (clear) {
+        static unsigned long long zero[1024 * 16];
+        if (cudaMemcpyToSymbol(bolt::g_stamps_topk, zero, sizeof(zero)) != cudaSuccess) return BOLT_ECUDA;
+    }
+    return BOLT_OK;
+}
+#endif
 
 extern "C" {
 

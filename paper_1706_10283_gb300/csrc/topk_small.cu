@@ -38,6 +38,10 @@
 
 namespace bolt {
 
+// phase stamps (diagnostic builds): 0 start, 1 scan done, 2 k-th bin, 3 kept,
+// 4 sorted list, 5 ticket; the last CTA: 6 loaded, 7 pool bound, 8 prefixes
+// checked, 9 gathered, 10 sorted, 11 end; 13: fast keep, 14: fast merge
+BOLT_STAMP_ARRAY(g_stamps_small);
 constexpr int kSmallThreads = 512;
 constexpr int kSmallWarps = kSmallThreads / 32;
 constexpr int kSmallChunk = 8;  // blocks per bulk copy
@@ -280,6 +284,7 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t q = blockIdx.y;
     const int G = gridDim.x, cta = blockIdx.x;
+    BOLT_STAMP(g_stamps_small, q, cta, 0);
 
     uint8_t *p = smem;
     uint32_t *hist = reinterpret_cast<uint32_t *>(p);
@@ -374,6 +379,7 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
     }
     if (failed && lane == 0) atomicOr(&misc[2], 1u);
     __syncthreads();
+    BOLT_STAMP(g_stamps_small, q, cta, 1);
     const bool bad = misc[2] != 0u;
     if (bad) {
         // let copies still in flight land before shared memory is reused
@@ -419,6 +425,7 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
             c_lt = below + below2;
         }
         const int64_t base = b0 * kBlockVecs;
+        BOLT_STAMP(g_stamps_small, q, cta, 2);
         // entries equal to T (the histogram still holds their count)
         const uint32_t n_le = c_lt + hist[hshift > 0 ? (T & ((1u << hshift) - 1u)) : T];
         // the code area is free now: room for nbc * M * 32 keys of 32 bits
@@ -430,6 +437,8 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
             // among those equal to T
             uint32_t *le = reinterpret_cast<uint32_t *>(region);
             small_keep_le(sums_s, L, T, le, wsum);
+            BOLT_STAMP(g_stamps_small, q, cta, 3);
+            BOLT_STAMP_VALUE(g_stamps_small, q, cta, 13, 1);
             small_rank_sort(le, (int)n_le, mine, (int)kk, [&](uint32_t key) {
                 return ((uint64_t)(key >> 16) << 32) | (uint64_t)(base + (int64_t)(key & 0xFFFFu));
             });
@@ -438,8 +447,10 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
             small_keep(L, T, kk - c_lt, s_of,
                        [&](uint32_t pos, int e) { kept[pos] = ((uint64_t)sums_s[e] << 32) | (uint64_t)(base + e); },
                        wsum);
+            BOLT_STAMP(g_stamps_small, q, cta, 3);
             small_rank_sort(kept, (int)kk, mine, (int)kk);
         }
+        BOLT_STAMP(g_stamps_small, q, cta, 4);
     }
     if (tid == 0) {
         ws.cnt[q * G + cta] = bad ? 0u : kk;
@@ -447,6 +458,7 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
     }
     __threadfence();
     __syncthreads();
+    BOLT_STAMP(g_stamps_small, q, cta, 5);
     if (tid == 0) misc[3] = (atomicAdd(&ws.ticket[q], 1u) == (uint32_t)(G - 1)) ? 1u : 0u;
     __syncthreads();
     if (misc[3] == 0) return;
@@ -513,6 +525,7 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
     for (int i = tid; i < kBins; i += kSmallThreads) hist[i] = 0;
     __syncthreads();
     const bool qbad = (misc[2] & 4u) != 0u;
+    BOLT_STAMP(g_stamps_small, q, cta, 6);
     const uint32_t total = misc[5];
     const int kout = qbad ? 0 : (int)min((uint32_t)k, total);
     bool sorted_done = false;
@@ -527,6 +540,7 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
             const uint32_t B = small_find(hist, (uint32_t)kout, misc, wsum, below);
             Tst = B;
             n_le = below + hist[B];
+            BOLT_STAMP(g_stamps_small, q, cta, 7);
             if (hshift > 0) {  // exact value inside bin B
                 const uint32_t mask = (1u << hshift) - 1u;
                 for (int i = tid; i < kBins; i += kSmallThreads) hist[i] = 0;
@@ -546,6 +560,8 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
                     atomicOr(&misc[6], 1u);
             __syncthreads();
             fast = misc[6] == 0u && n_le <= (uint32_t)P;
+            BOLT_STAMP(g_stamps_small, q, cta, 8);
+            BOLT_STAMP_VALUE(g_stamps_small, q, cta, 14, fast ? 1 : 0);
         }
         if (fast) {
             // the pool's keys with s' <= T* (n_le of them), then the kout smallest
@@ -554,6 +570,7 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
                 npool,
                 [&](int e) { return e < G * kSmallPrefix && in_pool(e) && (uint32_t)(pre[e] >> 32) <= Tst; },
                 [&](int e) { return pre[e]; }, fin, wsum);
+            BOLT_STAMP(g_stamps_small, q, cta, 9);
             if (kout <= 256) {
                 small_rank_sort(fin, (int)n_le, fin + P, kout);
                 __syncthreads();
@@ -642,6 +659,7 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
             small_bitonic(fin, P);
         }
     }
+    BOLT_STAMP(g_stamps_small, q, cta, 10);
     for (int r = tid; r < k; r += kSmallThreads) {
         if (r < kout) {
             const uint32_t sp = (uint32_t)(fin[r] >> 32);
@@ -652,7 +670,24 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
             out_idx[q * k + r] = qbad ? -2 : -1;
         }
     }
+    BOLT_STAMP(g_stamps_small, q, cta, 11);
 }
+
+#ifdef BOLT_PHASE_STAMPS
+}  // namespace bolt
+// Copies the shared-memory kernel's stamps (1024 CTAs x 16 slots) to host
+// and, with clear != 0, zeroes them (diagnostic builds only).
+extern "C" int bolt_debug_stamps_small(unsigned long long *host, int clear) {
+    if (cudaMemcpyFromSymbol(host, bolt::g_stamps_small, sizeof(unsigned long long) * 1024 * 16) != cudaSuccess)
+        return BOLT_ECUDA;
+    if (clear) {
+        static unsigned long long zero[1024 * 16];
+        if (cudaMemcpyToSymbol(bolt::g_stamps_small, zero, sizeof(zero)) != cudaSuccess) return BOLT_ECUDA;
+    }
+    return BOLT_OK;
+}
+namespace bolt {
+#endif
 
 // ------------------------------------------------------------------ host side
 static size_t small_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
