@@ -918,33 +918,34 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     const uint32_t bfin = total > (uint32_t)kRankSortMax ? vmisc[5] : 0xFFFFFFFFu;
     uint64_t *mk = reinterpret_cast<uint64_t *>(smem);
     uint32_t kept_all = 0;
+    constexpr int kGather = 8;  // keys per thread per gather round: 4,096 keys in one round at 512 threads
     int steps = 0;  // binary-search steps over the G slots
     while ((1 << steps) < G) ++steps;
-    for (uint32_t e0 = 0; e0 < total; e0 += 4 * T) {
-        // slot of entry e: the last c with off[c] <= e (four searches in step)
-        uint32_t e[4];
-        int lo[4];
+    for (uint32_t e0 = 0; e0 < total; e0 += kGather * T) {
+        // slot of entry e: the last c with off[c] <= e (kGather searches in step)
+        uint32_t e[kGather];
+        int lo[kGather];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kGather; ++u) {
             e[u] = e0 + u * T + tid;
             lo[u] = 0;
         }
         for (int bit = steps - 1; bit >= 0; --bit) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kGather; ++u) {
                 const int mid = lo[u] + (1 << bit);
                 if (mid < G && off[mid] <= e[u]) lo[u] = mid;
             }
         }
-        uint64_t v[4];
+        uint64_t v[kGather];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < kGather; ++u)
             v[u] = e[u] < total ? __ldcg(slots + lo[u] * slot_len + 1 + (e[u] - off[lo[u]])) : ~0ull;
         // kept keys: warp ballots counted, a prefix over the warps, then the
         // writes (no shared-memory atomics)
-        uint32_t bal[4], cw = 0;
+        uint32_t bal[kGather], cw = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kGather; ++u) {
             bal[u] = __ballot_sync(0xFFFFFFFFu, v[u] != ~0ull && ((uint32_t)(v[u] >> 32) >> hshift) <= bfin);
             cw += __popc(bal[u]);
         }
@@ -957,7 +958,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             tot += c;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kGather; ++u) {
             if (bal[u] & (1u << lane)) mk[pos + __popc(bal[u] & lanemask_lt())] = v[u];
             pos += __popc(bal[u]);
         }
