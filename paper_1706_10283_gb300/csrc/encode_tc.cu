@@ -132,12 +132,18 @@ __device__ __forceinline__ uint32_t swz_off(int r, int j) {
 // Warp roles:
 //   warp 0        MMA issuer (one thread) and owner of the tensor memory
 //   warp 1        bulk-copy producer: 128 x 32 fp32 chunks into a ring of kWsX stages
-//   warps 2..5    converters, one row per thread: fp32 -> bf16 hi/lo tiles
-//                 (core-matrix layout) and the squared norm of every subspace
-//   warps 6..21   epilogue, four warps per tensor-memory lane quarter (warp
-//                 id mod 4), each with a share of the chunk's subspaces: scores
-//                 from tensor memory, argmin with the margin, fp32 re-check of
-//                 near ties (x read from global memory), codes
+//   warps 2..9    converters in two groups of four that take alternate chunks,
+//                 one row per thread: fp32 -> bf16 hi/lo tiles (core-matrix
+//                 layout) and the squared norm of every subspace
+//   warps 10..25  epilogue in four groups of four (one warp per tensor-memory
+//                 lane quarter, warp id mod 4); group g takes chunks g, g + 4,
+//                 ..., every subspace of them: scores from tensor memory, argmin
+//                 with the margin, fp32 re-check of near ties (x read from
+//                 global memory), codes
+// Each role's warps work on different chunks at once (a warp of a group has
+// two or four chunk periods for one chunk), so the latency of one chunk's
+// chain of shared-memory, tensor-memory and shuffle steps is covered by the
+// other groups' chunks.
 // The roles run ahead of one another through rings of mbarriers:
 //   xfull/xfree   fp32 stage   (producer -> converters -> producer)
 //   afull/afree   bf16 tiles   (converters -> MMA -> converters)
@@ -150,12 +156,14 @@ __device__ __forceinline__ uint32_t swz_off(int r, int j) {
 // Ring depths: the bf16 tiles and the accumulators are held until the MMAs
 // that use them complete (about 2 us after issue), so both rings hold several
 // chunks; the fp32 stages cover the copy latency.
-constexpr int kWsWarps = 22;
+constexpr int kConvGroups = 2;  // converter groups (alternate chunks)
+constexpr int kEpiGroups = 4;   // epilogue groups (every fourth chunk)
+constexpr int kWsWarps = 2 + 4 * kConvGroups + 4 * kEpiGroups;
 constexpr int kWsThreads = kWsWarps * 32;
 constexpr int kWsXMax = 6;  // staged fp32 chunks (as many as fit, at least 2)
 constexpr int kWsA = 4;     // converted bf16 chunks
 constexpr int kMmaWarp = 0, kProducerWarp = 1;
-constexpr int kConvWarp0 = 2, kConvWarps = 4, kEpiWarp0 = 6, kEpiWarps = 16, kEpiParts = kEpiWarps / 4;
+constexpr int kConvWarp0 = 2, kConvWarps = 4 * kConvGroups, kEpiWarp0 = kConvWarp0 + kConvWarps;
 constexpr int kABytes = 2 * kTcRows * kTcKC * 2;  // hi tile + lo tile of one chunk, 16 KB
 constexpr int kMaxWsB = 8;
 constexpr size_t kWsSmemCap = 224 * 1024;
@@ -168,8 +176,7 @@ template <int S>
 struct WsShape {
     using SH = TcShape<S>;
     static constexpr int NB = SH::COLS >= 128 ? 4 : 8;  // accumulator slots (at most 512 columns)
-    // subspaces of a chunk per epilogue part (SPC / kEpiParts, at least 1)
-    static constexpr int PER_PART = SH::SPC >= kEpiParts ? SH::SPC / kEpiParts : 1;
+    static_assert(NB % kEpiGroups == 0 && NB % kConvGroups == 0, "a group's chunks keep their slots");
     static constexpr int NCOLS_USED = NB * SH::COLS;
     static constexpr int NCOL = NCOLS_USED < 32 ? 32 : NCOLS_USED;  // power of two
 };
@@ -314,17 +321,17 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     if (tid == 0) {
         for (int i = 0; i < kWsXMax; ++i) {
             mbar_init(&bars[kBarXFull + i], 1);
-            mbar_init(&bars[kBarXFree + i], kConvWarps);
+            mbar_init(&bars[kBarXFree + i], 4);
         }
         for (int i = 0; i < kWsA; ++i) {
-            mbar_init(&bars[kBarAFull + i], kConvWarps);
+            mbar_init(&bars[kBarAFull + i], 4);
             mbar_init(&bars[kBarAFree + i], 1);
         }
         for (int i = 0; i < kMaxWsB; ++i) {
             mbar_init(&bars[kBarAccFull + i], 1);
-            mbar_init(&bars[kBarAccFree + i], kEpiWarps);
-            mbar_init(&bars[kBarNFull + i], kConvWarps);
-            mbar_init(&bars[kBarNFree + i], kEpiWarps);
+            mbar_init(&bars[kBarAccFree + i], 4);
+            mbar_init(&bars[kBarNFull + i], 4);
+            mbar_init(&bars[kBarNFree + i], 4);
         }
         tslot[1] = 0;
         tslot[2] = 0;
@@ -344,19 +351,27 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     // This CTA's chunks in order: q -> tile blockIdx.x + (q / nchunks) * gridDim.x, dims (q % nchunks) * 32.
     const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const uint32_t total = (uint32_t)(my_tiles * nchunks);
-    auto q_tile = [&](uint32_t q) -> int64_t { return blockIdx.x + (int64_t)(q / nchunks) * gridDim.x; };
     unsigned my_rechecks = 0;
 
     if (warp == kProducerWarp) {
         // ---------------- producer
         if (lane == 0) {
-            uint32_t q = 0;
+            // stage xs = q % kWsX of round q / kWsX; chunk c of tile t (counters, no divisions)
+            uint32_t q = 0, xs = 0, xround = 0;
+            int c = 0;
+            int64_t t = blockIdx.x;
             for (; q < total; ++q) {
-                const uint32_t xs = q % kWsX;
-                if (q >= kWsX && !ws_wait(&bars[kBarXFree + xs], ((q / kWsX) - 1) & 1u, fail, wait_ns)) break;
+                if (q >= (uint32_t)kWsX && !ws_wait(&bars[kBarXFree + xs], (xround - 1) & 1u, fail, wait_ns)) break;
                 mbar_arrive_expect_tx(&bars[kBarXFull + xs], (uint32_t)kTcStageBytes);
-                tma_load_2d(X32 + (size_t)xs * kTcStageBytes, &xmap, (int)(q % nchunks) * kTcKC,
-                            (int)(q_tile(q) * kTcRows), &bars[kBarXFull + xs]);
+                tma_load_2d(X32 + (size_t)xs * kTcStageBytes, &xmap, c * kTcKC, (int)(t * kTcRows), &bars[kBarXFull + xs]);
+                if (++xs == (uint32_t)kWsX) {
+                    xs = 0;
+                    ++xround;
+                }
+                if (++c == nchunks) {
+                    c = 0;
+                    t += gridDim.x;
+                }
             }
             // copies issued but perhaps not consumed (after a failure): let them land
             if (*fail)
@@ -367,24 +382,27 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         // ---------------- MMA issuer
         if (lane == 0) {
             constexpr uint32_t kIdesc = idesc_bf16_f32(kTcRows, SH::NS);
-            const uint32_t a_addr = smem_u32(A), b_addr = smem_u32(B);
+            // Descriptors of the first A tile and of the first B slice; the
+            // others differ only in the start-address field (address >> 4 in
+            // bits 0-13, below 2^14 for every shared-memory address), so they
+            // are these plus the byte offset >> 4.
+            const uint64_t a_desc0 = umma_desc(smem_u32(A), (kTcRows / 8) * 128, 128);
+            const uint64_t b_desc0 = umma_desc(smem_u32(B), (SH::NS / 8) * 128, 128);
             uint32_t q = 0;
+            int c = 0;  // chunk q % nchunks
             for (; q < total; ++q) {
                 const uint32_t a = q % kWsA, bb = q % NB;
                 if (!ws_wait(&bars[kBarAFull + a], (q / kWsA) & 1u, fail, wait_ns)) break;
                 if (q >= (uint32_t)NB && !ws_wait(&bars[kBarAccFree + bb], ((q / NB) - 1) & 1u, fail, wait_ns)) break;
                 tc_fence_after();
-                const int c = (int)(q % nchunks);
-                const uint32_t a_base = a_addr + a * kABytes;
                 const uint32_t d_base = tmem + bb * SH::COLS;
 #pragma unroll
                 for (int tl = 0; tl < 2; ++tl) {
                     const int T = c * 2 + tl;
-                    const uint32_t a_off = tl * (2 * (kTcRows / 8) * 128);
-                    const uint64_t ah = umma_desc(a_base + a_off, (kTcRows / 8) * 128, 128);
-                    const uint64_t al = umma_desc(a_base + kTcRows * kTcKC * 2 + a_off, (kTcRows / 8) * 128, 128);
-                    const uint64_t bh = umma_desc(b_addr + T * SH::SLICE_BYTES, (SH::NS / 8) * 128, 128);
-                    const uint64_t bl = umma_desc(b_addr + (nslices + T) * SH::SLICE_BYTES, (SH::NS / 8) * 128, 128);
+                    const uint64_t ah = a_desc0 + ((a * kABytes + tl * (2 * (kTcRows / 8) * 128)) >> 4);
+                    const uint64_t al = ah + ((kTcRows * kTcKC * 2) >> 4);
+                    const uint64_t bh = b_desc0 + ((uint32_t)(T * SH::SLICE_BYTES) >> 4);
+                    const uint64_t bl = b_desc0 + ((uint32_t)((nslices + T) * SH::SLICE_BYTES) >> 4);
                     const uint32_t dcol = S <= 16 ? tl * SH::NS : 0;
                     tc_mma(d_base + dcol, ah, bh, kIdesc, (S > 16 && tl > 0) ? 1u : 0u);
                     tc_mma(d_base + dcol, ah, bl, kIdesc, 1u);
@@ -392,16 +410,19 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 }
                 tc_commit(&bars[kBarAFree + a]);
                 tc_commit(&bars[kBarAccFull + bb]);
+                if (++c == nchunks) c = 0;
             }
             // MMAs still in flight after a failure: let them finish before the tensor memory is freed
             if (*fail && q > 0) mbar_wait_bounded(&bars[kBarAccFull + (q - 1) % NB], ((q - 1) / NB) & 1u, kTcWait / 10);
         }
     } else if (warp < kEpiWarp0) {
         // ---------------- converters
-        const int r = (warp - kConvWarp0) * 32 + lane;
-        for (uint32_t q = 0; q < total; ++q) {
-            const uint32_t xs = q % kWsX, a = q % kWsA, bb = q % NB;
-            bool ok = ws_wait(&bars[kBarXFull + xs], (q / kWsX) & 1u, fail, wait_ns);
+        const int r = ((warp - kConvWarp0) & 3) * 32 + lane;
+        const uint32_t g = (uint32_t)((warp - kConvWarp0) >> 2);  // this warp's group: chunks g, g + kConvGroups, ...
+        uint32_t xs = g, xround = 0;                               // stage q % kWsX of round q / kWsX
+        for (uint32_t q = g; q < total; q += kConvGroups) {
+            const uint32_t a = q % kWsA, bb = q % NB;
+            bool ok = ws_wait(&bars[kBarXFull + xs], xround & 1u, fail, wait_ns);
             if (ok && q >= kWsA) ok = ws_wait(&bars[kBarAFree + a], ((q / kWsA) - 1) & 1u, fail, wait_ns);
             if (ok && q >= (uint32_t)NB) ok = ws_wait(&bars[kBarNFree + bb], ((q / NB) - 1) & 1u, fail, wait_ns);
             if (!__all_sync(0xFFFFFFFFu, ok)) break;
@@ -437,127 +458,108 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 mbar_arrive(&bars[kBarXFree + xs]);
                 mbar_arrive(&bars[kBarNFull + bb]);
             }
+            xs += kConvGroups;
+            if (xs >= (uint32_t)kWsX) {
+                xs -= kWsX;
+                ++xround;
+            }
         }
     } else {
         // ---------------- epilogue
-        const int ew = warp - kEpiWarp0, lq = warp & 3, part = ew / 4;
-        const bool pad_writer = ew == 0;  // writes the padding codes of the last block
-        const int r = lq * 32 + lane;  // this warp's tensor-memory lanes
-        constexpr int PP = WS::PER_PART;
-        constexpr int QB = 1;  // chunks per iteration
-        const int i0 = part * PP;            // this part's first subspace of a chunk
-        const bool has_work = i0 < SH::SPC;
-        // tile and chunk of q0, advanced with q0 (no divisions in the loop)
-        int64_t t_cur = blockIdx.x;
-        int c_cur = 0;
-        for (uint32_t q0 = 0; q0 < total; q0 += QB) {
-            const uint32_t nq = min((uint32_t)QB, total - q0);
-            bool ok = true;
-            for (uint32_t j = 0; j < nq; ++j) {
-                const uint32_t q = q0 + j, bb = q % NB;
-                if (ok) ok = ws_wait(&bars[kBarAccFull + bb], (q / NB) & 1u, fail, wait_ns);
-                if (ok) ok = ws_wait(&bars[kBarNFull + bb], (q / NB) & 1u, fail, wait_ns);
-            }
+        const int lq = warp & 3;                        // tensor-memory lane quarter
+        const uint32_t g = (uint32_t)((warp - kEpiWarp0) >> 2);  // chunks g, g + kEpiGroups, ...
+        const bool pad_writer = lq == 0;  // writes the padding codes of the last block
+        const int r = lq * 32 + lane;     // this thread's row of the tile
+        constexpr int PL = SH::SPC >= 2 ? 2 : 1;  // subspaces per tensor-memory load
+        // tile and chunk of q, advanced with q (no divisions in the loop)
+        int64_t t = blockIdx.x + (int64_t)(g / nchunks) * gridDim.x;
+        int c = (int)(g % nchunks);
+        for (uint32_t q = g; q < total; q += kEpiGroups) {
+            const uint32_t bb = q % NB;
+            bool ok = ws_wait(&bars[kBarAccFull + bb], (q / NB) & 1u, fail, wait_ns);
+            if (ok) ok = ws_wait(&bars[kBarNFull + bb], (q / NB) & 1u, fail, wait_ns);
             if (!__all_sync(0xFFFFFFFFu, ok)) break;
             tc_fence_after();
-            if (has_work) {
-                // this part's accumulator columns of the nq chunks: all loads before the waits
-                float d[QB][PP][16];
+            const int64_t v = t * kTcRows + r;
+            const bool valid = v < n;
 #pragma unroll
-                for (int j = 0; j < QB; ++j)
+            for (int i0 = 0; i0 < SH::SPC; i0 += PL) {
+                float d[PL][16];
 #pragma unroll
-                    for (int ii = 0; ii < PP; ++ii)
-                        if ((uint32_t)j < nq)
-                            tmem_ld16_nowait(tmem + ((q0 + j) % NB) * SH::COLS + ((uint32_t)(lq * 32) << 16) +
-                                                 (uint32_t)((i0 + ii) * 16),
-                                             d[j][ii]);
+                for (int ii = 0; ii < PL; ++ii)
+                    tmem_ld16_nowait(tmem + bb * SH::COLS + ((uint32_t)(lq * 32) << 16) + (uint32_t)((i0 + ii) * 16),
+                                     d[ii]);
 #pragma unroll
-                for (int j = 0; j < QB; ++j)
+                for (int ii = 0; ii < PL; ++ii) tmem_wait_ld(d[ii]);
 #pragma unroll
-                    for (int ii = 0; ii < PP; ++ii) tmem_wait_ld(d[j][ii]);
-                static_assert(QB == 1, "one chunk per epilogue iteration");
+                for (int ii = 0; ii < PL; ++ii) {
+                    const int i = i0 + ii;
+                    const int m = c * SH::SPC + i;
+                    const float4 *c2 = reinterpret_cast<const float4 *>(cn2 + m * kK);
+                    float sc[16];
 #pragma unroll
-                for (int j = 0; j < QB; ++j) {
-                    if ((uint32_t)j >= nq) break;
-                    const uint32_t q = q0 + j, bb = q % NB;
-                    const int64_t t = t_cur;
-                    const int c = c_cur;
-                    const int64_t v = t * kTcRows + r;
-                    const bool valid = v < n;
-#pragma unroll
-                    for (int ii = 0; ii < PP; ++ii) {
-                        const int i = i0 + ii;
-                        const int m = c * SH::SPC + i;
-                        const float4 *c2 = reinterpret_cast<const float4 *>(cn2 + m * kK);
-                        float sc[16];
-#pragma unroll
-                        for (int k4 = 0; k4 < 4; ++k4) {
-                            const float4 cc = c2[k4];
-                            sc[4 * k4 + 0] = __fmaf_rn(-2.0f, d[j][ii][4 * k4 + 0], cc.x);
-                            sc[4 * k4 + 1] = __fmaf_rn(-2.0f, d[j][ii][4 * k4 + 1], cc.y);
-                            sc[4 * k4 + 2] = __fmaf_rn(-2.0f, d[j][ii][4 * k4 + 2], cc.z);
-                            sc[4 * k4 + 3] = __fmaf_rn(-2.0f, d[j][ii][4 * k4 + 3], cc.w);
-                        }
-                        // minimum as a tree (fminf is exact: any order gives the same value)
-                        float mn[8];
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) mn[k] = fminf(sc[k], sc[k + 8]);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) mn[k] = fminf(mn[k], mn[k + 4]);
-                        const float best = fminf(fminf(mn[0], mn[2]), fminf(mn[1], mn[3]));
-                        // margin 4 (eps + eta) as a quadratic in X with per-codebook coefficients
-                        const float Xn = sqrt_approx(nrm[((size_t)bb * SH::SPC + i) * kTcRows + r]) * 1.0001f + 1e-30f;
-                        const float4 pc = reinterpret_cast<const float4 *>(cmax)[m];
-                        const float lim = best + __fmaf_rn(__fmaf_rn(pc.z, Xn, pc.y), Xn, pc.x);
-                        uint32_t mask = 0;
-#pragma unroll
-                        for (int k = 0; k < 16; ++k) mask |= (sc[k] <= lim ? 1u : 0u) << k;
-                        if (!(lim < INFINITY)) mask = 0xFFFFu;  // non-finite scores: check every centroid
-                        // a unique candidate is the tensor-core minimum itself
-                        uint32_t code = (uint32_t)(__ffs(mask) - 1) & 15u;
-                        if (__popc(mask) > 1 && valid) {
-                            const float *xv = Xg + v * J + (int64_t)m * S;
-                            float bd = INFINITY;
-                            code = 0;
-                            for (int k = 0; k < 16; ++k) {
-                                if (!(mask & (1u << k))) continue;
-                                const float dk = canon_dist_g(xv, C + ((size_t)m * kK + k) * S, S);
-                                if (dk < bd) {
-                                    bd = dk;
-                                    code = (uint32_t)k;
-                                }
-                            }
-                            ++my_rechecks;
-                        }
-                        if (!valid) code = 0;
-                        uint32_t word = code << (4 * (lane & 7));
-                        word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
-                        word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
-                        word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
-                        if ((lane & 7) == 0) codes[((v >> 8) * M + m) * kRowWords + ((v & 255) >> 3)] = word;
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        const float4 cc = c2[k4];
+                        sc[4 * k4 + 0] = __fmaf_rn(-2.0f, d[ii][4 * k4 + 0], cc.x);
+                        sc[4 * k4 + 1] = __fmaf_rn(-2.0f, d[ii][4 * k4 + 1], cc.y);
+                        sc[4 * k4 + 2] = __fmaf_rn(-2.0f, d[ii][4 * k4 + 2], cc.z);
+                        sc[4 * k4 + 3] = __fmaf_rn(-2.0f, d[ii][4 * k4 + 3], cc.w);
                     }
+                    // minimum as a tree (fminf is exact: any order gives the same value)
+                    float mn[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) mn[k] = fminf(sc[k], sc[k + 8]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) mn[k] = fminf(mn[k], mn[k + 4]);
+                    const float best = fminf(fminf(mn[0], mn[2]), fminf(mn[1], mn[3]));
+                    // margin 4 (eps + eta) as a quadratic in X with per-codebook coefficients
+                    const float Xn = sqrt_approx(nrm[((size_t)bb * SH::SPC + i) * kTcRows + r]) * 1.0001f + 1e-30f;
+                    const float4 pc = reinterpret_cast<const float4 *>(cmax)[m];
+                    const float lim = best + __fmaf_rn(__fmaf_rn(pc.z, Xn, pc.y), Xn, pc.x);
+                    uint32_t mask = 0;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) mask |= (sc[k] <= lim ? 1u : 0u) << k;
+                    if (!(lim < INFINITY)) mask = 0xFFFFu;  // non-finite scores: check every centroid
+                    // a unique candidate is the tensor-core minimum itself
+                    uint32_t code = (uint32_t)(__ffs(mask) - 1) & 15u;
+                    if (__popc(mask) > 1 && valid) {
+                        const float *xv = Xg + v * J + (int64_t)m * S;
+                        float bd = INFINITY;
+                        code = 0;
+                        for (int k = 0; k < 16; ++k) {
+                            if (!(mask & (1u << k))) continue;
+                            const float dk = canon_dist_g(xv, C + ((size_t)m * kK + k) * S, S);
+                            if (dk < bd) {
+                                bd = dk;
+                                code = (uint32_t)k;
+                            }
+                        }
+                        ++my_rechecks;
+                    }
+                    if (!valid) code = 0;
+                    uint32_t word = code << (4 * (lane & 7));
+                    word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
+                    word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
+                    word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
+                    if ((lane & 7) == 0) codes[((v >> 8) * M + m) * kRowWords + ((v & 255) >> 3)] = word;
                 }
             }
             tc_fence_before();
             __syncwarp();
-            for (uint32_t j = 0; j < nq; ++j) {
-                const uint32_t q = q0 + j, bb = q % NB;
-                if (lane == 0) {
-                    mbar_arrive(&bars[kBarAccFree + bb]);
-                    mbar_arrive(&bars[kBarNFree + bb]);
-                }
-                const int64_t t = t_cur;
-                const int c = c_cur;
-                if (pad_writer && t == ntiles - 1 && c == nchunks - 1 && ((t + 1) * kTcRows) % kBlockVecs != 0) {
-                    // second half of the last block holds padding vectors: code 0
-                    const int64_t blk = (t * kTcRows) >> 8;
-                    for (int ee = lane; ee < M * 16; ee += 32)
-                        codes[(blk * M + ee / 16) * kRowWords + 16 + (ee % 16)] = 0u;
-                }
-                if (++c_cur == nchunks) {
-                    c_cur = 0;
-                    t_cur += gridDim.x;
-                }
+            if (lane == 0) {
+                mbar_arrive(&bars[kBarAccFree + bb]);
+                mbar_arrive(&bars[kBarNFree + bb]);
+            }
+            if (pad_writer && t == ntiles - 1 && c == nchunks - 1 && ((t + 1) * kTcRows) % kBlockVecs != 0) {
+                // second half of the last block holds padding vectors: code 0
+                const int64_t blk = (t * kTcRows) >> 8;
+                for (int ee = lane; ee < M * 16; ee += 32)
+                    codes[(blk * M + ee / 16) * kRowWords + 16 + (ee % 16)] = 0u;
+            }
+            c += kEpiGroups;
+            while (c >= nchunks) {
+                c -= nchunks;
+                t += gridDim.x;
             }
         }
     }
