@@ -228,22 +228,52 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return y;
 }
 
-// Canonical fp32 distance of x's subvector (s contiguous floats in global
-// memory) to one centroid c.
-__device__ __forceinline__ float canon_dist_g(const float *__restrict__ x, const float *__restrict__ c, int s) {
-    float acc = 0.0f;
-    for (int j = 0; j < s; ++j) {
-        const float t = __fsub_rn(__ldg(x + j), __ldg(c + j));
-        acc = __fmaf_rn(t, t, acc);
+// Packed fp32 pairs (each half rounds exactly like the scalar instruction).
+__device__ __forceinline__ uint64_t tc_f2_sub(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t tc_f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t tc_f2_pack(float lo, float hi) {
+    return (uint64_t)__float_as_uint(lo) | ((uint64_t)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float tc_f2_lo(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float tc_f2_hi(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+
+// Canonical fp32 squared distances of x's subvector xr to the candidate
+// centroids (bits of mask) of one codebook cb (16 x S floats), in increasing
+// index order; the smallest wins, the lower index on ties.
+template <int S>
+__device__ __forceinline__ uint32_t recheck_argmin(const float (&xr)[S], const float *cb, uint32_t mask) {
+    float bd = INFINITY;
+    uint32_t code = 0;
+    for (uint32_t mm = mask; mm; mm &= mm - 1) {
+        const int k = __ffs(mm) - 1;
+        const float *cv = cb + k * S;
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const float t = __fsub_rn(xr[j], cv[j]);
+            acc = __fmaf_rn(t, t, acc);
+        }
+        if (acc < bd) {
+            bd = acc;
+            code = (uint32_t)k;
+        }
     }
-    return acc;
+    return code;
 }
 
 template <int S>
 __global__ void __launch_bounds__(kWsThreads, 1)
     encode_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float *__restrict__ Xg, int64_t n, int32_t J,
                      int32_t M, const float *__restrict__ C, uint32_t *__restrict__ codes,
-                     unsigned long long *__restrict__ n_rechecked, int kWsX, uint64_t wait_ns) {
+                     unsigned long long *__restrict__ n_rechecked, int kWsX, int c_smem, uint64_t wait_ns) {
     using SH = TcShape<S>;
     using WS = WsShape<S>;
     constexpr int NB = WS::NB;
@@ -253,7 +283,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     const int nchunks = J / kTcKC;
 
     // shared memory: fp32 stages (1024-aligned, swizzled) | bf16 A tiles | B slices | norms | ||c||^2 |
-    //                margin coefficients | barriers | slots
+    //                margin coefficients | fp32 centroids (when c_smem) | barriers | slots
     uint8_t *p = tsm + ((1024u - (smem_u32(tsm) & 1023u)) & 1023u);
     uint8_t *X32 = p;
     p += kWsX * kTcStageBytes;
@@ -267,12 +297,16 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     p += (size_t)M * kK * 4;
     float *cmax = reinterpret_cast<float *>(p);  // [M][4]: margin polynomial p0, p1, p2 (rounded up)
     p += (size_t)M * 4 * 4;
+    float *csm = reinterpret_cast<float *>(p);  // [M][16][S] fp32 centroids for the re-check
+    if (c_smem) p += (size_t)M * kK * S * 4;
     uint64_t *bars = reinterpret_cast<uint64_t *>(p);
     p += kBarCount * 8;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(p);  // [0] TMEM base, [1] rechecks, [2] failure
     volatile uint32_t *fail = tslot + 2;
 
     // ---- one-time set-up: norms, margin coefficients and the bf16 B slices
+    if (c_smem)
+        for (int e = tid; e < M * kK * S; e += kWsThreads) csm[e] = C[e];
     for (int mk = tid; mk < M * kK; mk += kWsThreads) {
         const float *c = C + (size_t)mk * S;
         float acc = 0.0f;
@@ -428,9 +462,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             if (!__all_sync(0xFFFFFFFFu, ok)) break;
             const uint8_t *xs_stage = X32 + (size_t)xs * kTcStageBytes;
             uint8_t *Ab = A + (size_t)a * kABytes;
-            float xn[SH::SPC];
+            uint64_t xn2[SH::SPC];  // squared norm of each subspace, even and odd dims
 #pragma unroll
-            for (int i = 0; i < SH::SPC; ++i) xn[i] = 0.0f;
+            for (int i = 0; i < SH::SPC; ++i) xn2[i] = 0ull;
 #pragma unroll
             for (int kc = 0; kc < kTcKC / 8; ++kc) {
                 const float4 lo = *reinterpret_cast<const float4 *>(xs_stage + swz_off(r, 8 * kc));
@@ -441,16 +475,18 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 for (int qq = 0; qq < 4; ++qq) {
                     h[qq] = __floats2bfloat162_rn(v[2 * qq], v[2 * qq + 1]);
                     const float2 hf = __bfloat1622float2(h[qq]);
-                    l[qq] = __floats2bfloat162_rn(v[2 * qq] - hf.x, v[2 * qq + 1] - hf.y);
+                    const uint64_t vv = tc_f2_pack(v[2 * qq], v[2 * qq + 1]);
+                    const uint64_t lv = tc_f2_sub(vv, tc_f2_pack(hf.x, hf.y));
+                    l[qq] = __floats2bfloat162_rn(tc_f2_lo(lv), tc_f2_hi(lv));
+                    xn2[(8 * kc + 2 * qq) / S] = tc_f2_fma(vv, vv, xn2[(8 * kc + 2 * qq) / S]);
                 }
                 *reinterpret_cast<uint4 *>(Ab + core_off(r, 8 * kc, kTcRows)) = *reinterpret_cast<const uint4 *>(h);
                 *reinterpret_cast<uint4 *>(Ab + kTcRows * kTcKC * 2 + core_off(r, 8 * kc, kTcRows)) =
                     *reinterpret_cast<const uint4 *>(l);
-#pragma unroll
-                for (int qq = 0; qq < 8; ++qq) xn[(8 * kc + qq) / S] = __fmaf_rn(v[qq], v[qq], xn[(8 * kc + qq) / S]);
             }
 #pragma unroll
-            for (int i = 0; i < SH::SPC; ++i) nrm[((size_t)bb * SH::SPC + i) * kTcRows + r] = xn[i];
+            for (int i = 0; i < SH::SPC; ++i)
+                nrm[((size_t)bb * SH::SPC + i) * kTcRows + r] = __fadd_rn(tc_f2_lo(xn2[i]), tc_f2_hi(xn2[i]));
             fence_proxy_async_smem();  // this thread's A tiles, for the tensor cores
             __syncwarp();
             if (lane == 0) {
@@ -497,13 +533,16 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     const int m = c * SH::SPC + i;
                     const float4 *c2 = reinterpret_cast<const float4 *>(cn2 + m * kK);
                     float sc[16];
+                    const uint64_t m2 = tc_f2_pack(-2.0f, -2.0f);
 #pragma unroll
                     for (int k4 = 0; k4 < 4; ++k4) {
                         const float4 cc = c2[k4];
-                        sc[4 * k4 + 0] = __fmaf_rn(-2.0f, d[ii][4 * k4 + 0], cc.x);
-                        sc[4 * k4 + 1] = __fmaf_rn(-2.0f, d[ii][4 * k4 + 1], cc.y);
-                        sc[4 * k4 + 2] = __fmaf_rn(-2.0f, d[ii][4 * k4 + 2], cc.z);
-                        sc[4 * k4 + 3] = __fmaf_rn(-2.0f, d[ii][4 * k4 + 3], cc.w);
+                        const uint64_t s01 = tc_f2_fma(m2, tc_f2_pack(d[ii][4 * k4 + 0], d[ii][4 * k4 + 1]), tc_f2_pack(cc.x, cc.y));
+                        const uint64_t s23 = tc_f2_fma(m2, tc_f2_pack(d[ii][4 * k4 + 2], d[ii][4 * k4 + 3]), tc_f2_pack(cc.z, cc.w));
+                        sc[4 * k4 + 0] = tc_f2_lo(s01);
+                        sc[4 * k4 + 1] = tc_f2_hi(s01);
+                        sc[4 * k4 + 2] = tc_f2_lo(s23);
+                        sc[4 * k4 + 3] = tc_f2_hi(s23);
                     }
                     // minimum as a tree (fminf is exact: any order gives the same value)
                     float mn[8];
@@ -523,17 +562,24 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     // a unique candidate is the tensor-core minimum itself
                     uint32_t code = (uint32_t)(__ffs(mask) - 1) & 15u;
                     if (__popc(mask) > 1 && valid) {
-                        const float *xv = Xg + v * J + (int64_t)m * S;
-                        float bd = INFINITY;
-                        code = 0;
-                        for (int k = 0; k < 16; ++k) {
-                            if (!(mask & (1u << k))) continue;
-                            const float dk = canon_dist_g(xv, C + ((size_t)m * kK + k) * S, S);
-                            if (dk < bd) {
-                                bd = dk;
-                                code = (uint32_t)k;
-                            }
+                        // canonical fp32 distances of the candidates, in increasing
+                        // index order (ties keep the lower index); x's subvector
+                        // (16-byte aligned: X is, rows are J % 32 == 0 floats, S % 4 == 0)
+                        // is read once
+                        const float4 *xv = reinterpret_cast<const float4 *>(Xg + v * J + (int64_t)m * S);
+                        float xr[S];
+#pragma unroll
+                        for (int j4 = 0; j4 < S / 4; ++j4) {
+                            const float4 t4 = __ldg(xv + j4);
+                            xr[4 * j4 + 0] = t4.x;
+                            xr[4 * j4 + 1] = t4.y;
+                            xr[4 * j4 + 2] = t4.z;
+                            xr[4 * j4 + 3] = t4.w;
                         }
+                        // one call site per address space, so that the shared-memory
+                        // copy is read with shared-memory loads
+                        code = c_smem ? recheck_argmin<S>(xr, csm + (size_t)m * kK * S, mask)
+                                      : recheck_argmin<S>(xr, C + (size_t)m * kK * S, mask);
                         ++my_rechecks;
                     }
                     if (!valid) code = 0;
@@ -605,11 +651,16 @@ static int launch_tc(const float *X, int64_t n, int32_t J, int32_t M, const floa
     const size_t fixed = 1024 + kWsA * (size_t)kABytes + 2 * (size_t)nslices * SH::SLICE_BYTES +
                          (size_t)WS::NB * SH::SPC * kTcRows * 4 + (size_t)M * kK * 4 + (size_t)M * 4 * 4 +
                          kBarCount * 8 + 16;
+    // fp32 centroids in shared memory for the re-check when they fit beside
+    // at least 3 fp32 stages (else it reads them from global memory)
+    const size_t cbytes = (size_t)M * kK * S * 4;
+    const int c_smem = fixed + cbytes + 3 * (size_t)kTcStageBytes <= kWsSmemCap ? 1 : 0;
+    const size_t fixed_c = fixed + (c_smem ? cbytes : 0);
     // fp32 stages: enough bulk copies in flight to cover the memory latency
     // (up to kWsXMax), within kWsSmemCap of shared memory; at least two
     int nx = kWsXMax;
-    while (nx > 2 && fixed + (size_t)nx * kTcStageBytes > kWsSmemCap) --nx;
-    const size_t smem = fixed + (size_t)nx * kTcStageBytes;
+    while (nx > 2 && fixed_c + (size_t)nx * kTcStageBytes > kWsSmemCap) --nx;
+    const size_t smem = fixed_c + (size_t)nx * kTcStageBytes;
     if (smem > kWsSmemCap) return launch_encode_fp32(X, n, J, M, C, codes, stream);
     auto kern = encode_tc_kernel<S>;
     int rc = ensure_smem((const void *)kern, smem);
@@ -629,7 +680,7 @@ static int launch_tc(const float *X, int64_t n, int32_t J, int32_t M, const floa
     if (rc) return rc;
     kern<<<(int)grid, kWsThreads, smem, stream>>>(map, X, n, J, M, C, reinterpret_cast<uint32_t *>(codes),
                                                   reinterpret_cast<unsigned long long *>(n_rechecked), nx,
-                                                  data_wait_limit_ns());
+                                                  c_smem, data_wait_limit_ns());
     return check_launch("encode_tc_kernel");
 }
 

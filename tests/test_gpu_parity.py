@@ -89,7 +89,9 @@ def test_encode_adversarial_ties(torch_cuda):
 
 
 TC_SHAPES = [(10_000, 32, 8), (1_037, 128, 16), (40, 256, 32), (513, 64, 4), (777, 64, 2), (3000, 512, 32),
-             (1, 128, 16), (129, 128, 16), (257, 128, 16), (20_000, 256, 32)]
+             (1, 128, 16), (129, 128, 16), (257, 128, 16), (20_000, 256, 32),
+             # centroids too large for the shared-memory copy: the re-check reads them from global memory
+             (3000, 1024, 32), (3000, 1024, 64)]
 
 
 @pytest.mark.parametrize("n,J,M", TC_SHAPES)
