@@ -1,13 +1,14 @@
 // Bolt scan d^ (Sec. 3.1, sum of the table entries the codes pick; Sec. 3.2
 // 8-bit tables and vectorized lookups) and the fused exact top-k used for
 // nearest-neighbour and maximum-inner-product search.
-#include "scan_core.cuh"
+#include "scan_tiles.cuh"
 #include "topk.cuh"
 
 namespace bolt {
 
 // ------------------------------------------------------------------ plain sums
-// One warp per (query, 256-vector block); lane w owns word w of every row.
+// One warp per (query, 256-vector block) (grid-stride); lane w owns word w of
+// every row.  Used for one query and for small scans.
 __global__ void __launch_bounds__(256) scan_sums_kernel(const uint32_t *__restrict__ codes, int64_t n, int32_t M,
                                                         const uint8_t *__restrict__ luts, int64_t nq,
                                                         uint16_t *__restrict__ sums) {
@@ -41,15 +42,30 @@ __global__ void __launch_bounds__(256) scan_sums_kernel(const uint32_t *__restri
     }
 }
 
+// Several queries: tiles of up to 8 queries (each code word prepared once per
+// tile), the (tile, block) tasks split evenly over one wave of CTAs
+// (scan_tiles.cuh).
 static int launch_scan_sums(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq,
                             uint16_t *sums, cudaStream_t stream) {
     if (n == 0 || nq == 0) return BOLT_OK;
-    const int64_t items = num_blocks(n) * nq;
-    int64_t grid = (items + 7) / 8;
-    const int64_t cap = (int64_t)device_sm_count() * 8;
-    if (cap > 0 && grid > cap) grid = cap;
-    scan_sums_kernel<<<(int)grid, 256, 0, stream>>>(reinterpret_cast<const uint32_t *>(codes), n, M, luts, nq, sums);
-    return check_launch("scan_sums_kernel");
+    const int qb = nq >= 8 ? 8 : nq >= 4 ? 4 : nq >= 2 ? 2 : 1;
+    const int64_t tile_tasks = (nq + qb - 1) / qb * num_blocks(n);
+    // one query, or too few tile tasks to give every SM one (with short
+    // codebook loops): one warp per (query, block) spreads the work wider
+    if (nq == 1 || (tile_tasks < device_sm_count() && M <= 32)) {
+        const int64_t items = num_blocks(n) * nq;
+        int64_t grid = (items + 7) / 8;
+        const int64_t cap = (int64_t)device_sm_count() * 8;
+        if (cap > 0 && grid > cap) grid = cap;
+        scan_sums_kernel<<<(int)grid, 256, 0, stream>>>(reinterpret_cast<const uint32_t *>(codes), n, M, luts, nq,
+                                                        sums);
+        return check_launch("scan_sums_kernel");
+    }
+    const TileOutSums16 out{sums};
+    const char *what = "scan sums (tile_scan_kernel)";
+    if (qb == 8) return launch_tile_scan<8>(codes, n, M, luts, nq, out, stream, what);
+    if (qb == 4) return launch_tile_scan<4>(codes, n, M, luts, nq, out, stream, what);
+    return launch_tile_scan<2>(codes, n, M, luts, nq, out, stream, what);
 }
 
 // ------------------------------------------------------------------ uint32 sums

@@ -163,6 +163,20 @@ def test_scan_sums_bitexact(torch_cuda, n, M):
         np.testing.assert_array_equal(got.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("n,M,nq", [(150_001, 16, 21), (40_000, 64, 6), (60_000, 8, 9), (3_000, 128, 2)])
+def test_scan_sums_query_tiles(torch_cuda, n, M, nq):
+    """Scans of several queries run over tiles of up to 8 queries (each code
+    word prepared once per tile) split evenly over the CTAs; ragged last
+    tiles, shares that span two tiles and a ragged last block, against the
+    oracle."""
+    torch = torch_cuda
+    rng = np.random.default_rng(n + M + nq)
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+    luts = rng.integers(0, 256, (nq, M, 16)).astype(np.uint8)
+    got = bolt.scan_l2(bolt.pack_codes(dev(torch, codes)), n, M, dev(torch, luts))
+    np.testing.assert_array_equal(got.cpu().numpy(), oracle.scan(codes, luts))
+
+
 @pytest.mark.parametrize("n,J,M", [(10_000, 32, 8), (1_037, 128, 16), (70_001, 64, 32), (300, 64, 64), (257, 16, 1)])
 def test_scan_float_bitexact(torch_cuda, n, J, M):
     """Bolt No Quantize: fp32 sums over the fp32 tables, bit-exact against
