@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-aux", action="store_true", help="skip the large-N and encode side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["topk1m", "topk50m", "topk8m_batch64", "encode10m", "encode10m_tc", "batch", "serve",
-                             "large50m", "accuracy"], default=None,
+                             "large50m", "accuracy", "matmul"], default=None,
                     help="profiling run: set up one workload and launch only its kernel a few times")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--graph-reps", type=int, default=0, help="also time graph replays of the launches")
@@ -348,6 +348,44 @@ def batch_64_on_50m(codes, C, quant):
     return {"workload": "serve_50m: 64 L2 top-100 queries in one bolt_topk call (multi-query pipeline)",
             "ms_per_call": round(ms_b, 4), "ms_per_query": round(ms_b / 64, 4),
             "distances_per_s": 64 * n / (ms_b * 1e-3)}
+
+
+def scan_sums_report(codes, C, quant, hbm_peak):
+    """The plain scan (uint16 sums, no top-k): one query over the 50M
+    database against the HBM roofline (codes read + sums written), and 1,000
+    queries over its first 1M vectors (tiles of 8 queries per code pass)
+    against the integer-ALU peak.  The 1,000-query sums of query 0 must equal
+    the one-query sums over the same vectors."""
+    import torch
+
+    from paper_1706_10283_gb300 import alu_peak, bolt, synth
+
+    cfg = synth.CONFIGS["serve_50m"]
+    n, J, M = cfg["n"], cfg["J"], cfg["M"]
+    a, b = quant[bolt.METRIC_L2]
+    Qs = torch.from_numpy(synth.mixture(1000, J, 79)).cuda()
+    luts = bolt.build_luts(Qs, C, bolt.METRIC_L2, a, b)
+    out1 = torch.empty((1, n), dtype=torch.uint16, device="cuda")
+    ms1 = _graph_ms(lambda s: bolt.scan_l2(codes, n, M, luts[:1], out=out1, stream=s), reps=10)
+    n2 = 1_000_000
+    codes2 = codes[:bolt.codes_bytes(n2, M)]
+    out2 = torch.empty((1000, n2), dtype=torch.uint16, device="cuda")
+    ms2 = _graph_ms(lambda s: bolt.scan_l2(codes2, n2, M, luts, out=out2, stream=s), reps=3)
+    same = bool(torch.equal(out2[0], out1[0, :n2]))
+    del out1, out2
+    torch.cuda.empty_cache()
+    bytes1 = n * M // 2 + 2 * n
+    lookups2 = 1000 * n2 * M
+    peak = alu_peak.lookups_per_s()
+    return {"workload": "bolt_scan_l2 (uint16 sums): 1 query over serve_50m; 1,000 queries over its first 1M vectors",
+            "one_query_50m": {"ms": round(ms1, 4), "bytes": bytes1,
+                              "achieved_GBps": round(bytes1 / (ms1 * 1e-3) / 1e9, 1), "peak_GBps": hbm_peak,
+                              "frac": round(bytes1 / (ms1 * 1e-3) / 1e9 / hbm_peak, 4)},
+            "queries_1000_on_1m": {"ms": round(ms2, 4), "lookups": lookups2,
+                                   "achieved_Tlookup_s": round(lookups2 / (ms2 * 1e-3) / 1e12, 3),
+                                   "peak_Tlookup_s": round(peak / 1e12, 3),
+                                   "frac": round(lookups2 / (ms2 * 1e-3) / peak, 4)},
+            "query0_sums_equal": same}
 
 
 def serving(codes50, C, quant, count=300, rates=(40.0, 80.0), slots=4, budget_gb=16.0):
@@ -938,6 +976,7 @@ def run_bolt(args, world, rank, local):
         line["mixture_1m"] = one_million_step(args, X, Q1, Xd, Qd, C, quant, hbm_peak, peak_kind)
         line["small_iid_l2"] = small_iid_step()
         line["batch_64_on_50m"] = batch_64_on_50m(codes50, C, quant)
+        line["scan_sums"] = scan_sums_report(codes50, C, quant, hbm_peak)
         line["accuracy_mixture_1m"] = accuracy_report(Xd, C, quant)
         del Xd
         line["serving"] = serving(codes50, C, quant)
@@ -995,6 +1034,16 @@ def run_only(args):
         plan.autotune()
         print("tiles:", plan.tuning(), flush=True)
         fn = lambda: plan.run()  # noqa: E731
+    elif args.only == "matmul":
+        mm = synth.CONFIGS["matmul_4096x512_100k"]
+        rows, n, J, M = mm["rows"], mm["n"], mm["J"], mm["M"]
+        B = synth.mixture_torch(n, J, seed=900)
+        CB = bolt.fit_codebooks(B[:50_000].contiguous(), M, 4, synth.kmeans_init_rows(50_000, 900))
+        aB, bB, _ = bolt.fit_quantizer(B[:256].contiguous(), CB, bolt.METRIC_DOT)
+        codesB = bolt.encode(B, CB)
+        A = torch.from_numpy(synth.iid(rows, J, 901)).cuda()
+        out = torch.empty((rows, n), dtype=torch.float32, device="cuda")
+        fn = lambda: bolt.approx_matmul(A, codesB, n, CB, aB, bB, out=out)  # noqa: E731
     elif args.only in ("encode10m", "encode10m_tc"):
         cfg = synth.CONFIGS["encode_10m"]
         n, J, M = 2_000_000, cfg["J"], cfg["M"]  # 2 GB of fp32 input: > L2, small for ncu

@@ -6,11 +6,11 @@
 // dequantization of Sec. 3.2).
 //
 // Tasks are (tile of QB queries, 256-vector code block) pairs in tile-major
-// order.  Every CTA owns an equal, contiguous share of them, so one wave of
-// CTAs does all the work with the same amount per CTA.  The grid has at
-// least as many CTAs as there are query tiles, so a share holds at most one
-// tile's worth of tasks and spans at most two tiles, whose tables the CTA
-// stages in shared memory.  The CTA's warps take the share's tasks in turn.
+// order.  Every CTA owns an equal, contiguous share of them, and the grid is
+// a whole number of waves of resident CTAs, so every SM does the same work.
+// The grid has at least as many CTAs as there are query tiles, so a share
+// holds at most one tile's worth of tasks and spans at most two tiles, whose
+// tables the CTA stages in shared memory.  The CTA's warps take the share's tasks in turn.
 // For a task, each code word of the block is prepared once and looked up in
 // the QB tables of the tile; code words are loaded PF codebooks ahead.
 #pragma once
@@ -121,9 +121,9 @@ __global__ void __launch_bounds__(kTileThreads) tile_scan_kernel(const uint32_t 
     }
 }
 
-// One wave: a multiple of the resident CTAs, at least one CTA per query tile
-// (so a share spans at most two tiles); small problems get fewer CTAs, so
-// that each has a task for every warp.
+// Whole waves: a multiple of the resident CTAs, at least one CTA per query
+// tile (so a share spans at most two tiles); small problems get fewer CTAs,
+// so that each has a task for every warp.
 template <int QB, class Out>
 int launch_tile_scan(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, Out out,
                      cudaStream_t s, const char *what) {
