@@ -14,45 +14,46 @@ namespace bolt {
 constexpr int kChunkRows = 2048;  // fixed row chunk of the deterministic mean reduction
 
 // ------------------------------------------------------------------ k-means
-// Partial fp64 sums of one fixed chunk of rows.  Thread t owns column t
-// (m = t / s, dim j = t % s) and adds the rows of the chunk in row order into
-// its 16 per-centroid sums, so the result does not depend on scheduling.
+// Partial fp64 sums of one fixed chunk of rows.  Thread t owns column
+// c = c0 + t (m = c / s, dim j = c % s) and adds the rows of the chunk in row
+// order into its 16 per-centroid sums, so the result does not depend on
+// scheduling.  The 16 sums (and, for j = 0, the 16 counts) live in shared
+// memory slots of that thread, indexed by the row's code: one fp64 add per
+// value.
 __global__ void kmeans_partial_kernel(const float *__restrict__ X, int64_t n, int32_t J, int32_t M,
                                       const uint32_t *__restrict__ codes, double *__restrict__ psum,
                                       uint32_t *__restrict__ pcnt) {
+    extern __shared__ double kms[];
+    const int T = blockDim.x, t = threadIdx.x;
+    double *sacc = kms;                                          // [kK][T]
+    uint32_t *scnt = reinterpret_cast<uint32_t *>(kms + kK * T);  // [kK][T]
     const int s = J / M;
     const int64_t chunk = blockIdx.x;
     const int64_t r0 = chunk * kChunkRows;
     const int64_t r1 = min(n, r0 + kChunkRows);
-    for (int c = threadIdx.x; c < J; c += blockDim.x) {
+    for (int c0 = 0; c0 < J; c0 += T) {
+        const int c = c0 + t;
+        if (c >= J) break;
         const int m = c / s, j = c % s;
-        double acc[kK];
-        uint32_t cnt[kK];
 #pragma unroll
         for (int k = 0; k < kK; ++k) {
-            acc[k] = 0.0;
-            cnt[k] = 0;
+            sacc[k * T + t] = 0.0;
+            scnt[k * T + t] = 0u;
         }
         for (int64_t v = r0; v < r1; ++v) {
             const int64_t b = v / kBlockVecs;
             const int r = (int)(v % kBlockVecs);
             const uint32_t word = codes[(b * M + m) * kRowWords + r / 8];
             const int code = (word >> (4 * (r % 8))) & 15;
-            const double x = (double)X[v * J + c];
-#pragma unroll
-            for (int k = 0; k < kK; ++k) {
-                if (k == code) {
-                    acc[k] += x;
-                    cnt[k] += 1;
-                }
-            }
+            sacc[code * T + t] += (double)X[v * J + c];
+            if (j == 0) scnt[code * T + t] += 1u;
         }
         double *dst = psum + chunk * (int64_t)J * kK;
 #pragma unroll
-        for (int k = 0; k < kK; ++k) dst[((int64_t)m * kK + k) * s + j] = acc[k];
+        for (int k = 0; k < kK; ++k) dst[((int64_t)m * kK + k) * s + j] = sacc[k * T + t];
         if (j == 0) {
 #pragma unroll
-            for (int k = 0; k < kK; ++k) pcnt[chunk * (int64_t)M * kK + m * kK + k] = cnt[k];
+            for (int k = 0; k < kK; ++k) pcnt[chunk * (int64_t)M * kK + m * kK + k] = scnt[k * T + t];
         }
     }
 }
@@ -245,7 +246,8 @@ static int kmeans_impl(const float *X, int64_t n, int32_t J, int32_t M, int32_t 
         rc = launch_encode_fp32(X, n, J, M, C, codes, s);
         if (rc) return rc;
         const int threads = J < 256 ? ((J + 31) / 32) * 32 : 256;
-        kmeans_partial_kernel<<<(unsigned)nchunks, threads, 0, s>>>(X, n, J, M, reinterpret_cast<uint32_t *>(codes),
+        const size_t smem = (size_t)threads * kK * (sizeof(double) + sizeof(uint32_t));
+        kmeans_partial_kernel<<<(unsigned)nchunks, threads, smem, s>>>(X, n, J, M, reinterpret_cast<uint32_t *>(codes),
                                                                    static_cast<double *>(dSum.p),
                                                                    static_cast<uint32_t *>(dCnt.p));
         rc = check_launch("kmeans_partial_kernel");
