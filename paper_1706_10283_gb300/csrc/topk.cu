@@ -1015,7 +1015,17 @@ int plan_topk(int64_t n, int32_t M, int32_t k, int64_t nq, TopkPlan *plan) {
     plan->small = 0;
     plan->nbc = 0;
     plan->mq = 0;
-    if (plan_topk_small(n, M, k, device_sm_count(), plan)) return BOLT_OK;
+    const int sms = device_sm_count();
+    // Tiny databases with several queries: fewer CTAs per query (still one
+    // per SM over all the queries), each with a few blocks, so the last CTA
+    // of a query merges fewer lists.  Applied only while a CTA keeps at most
+    // 8 blocks.
+    if (nq > 1 && sms > 0) {
+        const int64_t nb = num_blocks(n), fill = (sms + nq - 1) / nq;
+        if (fill < nb && fill < sms && (nb + fill - 1) / fill <= 8 && plan_topk_small(n, M, k, sms, plan, fill))
+            return BOLT_OK;
+    }
+    if (plan_topk_small(n, M, k, sms, plan)) return BOLT_OK;
     int rc = plan_topk_stream(n, M, k, plan);
     if (rc) return rc;
     // several queries share each code pass in the multi-query pipeline; a

@@ -50,7 +50,8 @@ int64_t topk_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k);
 TopkWS carve_topk_ws(void *ws, const TopkPlan &plan, int64_t nq, int32_t k);
 size_t topk_header_bytes(int64_t nq);  // ticket/status + histograms (zeroed per call)
 
-bool plan_topk_small(int64_t n, int32_t M, int32_t k, int sms, TopkPlan *plan);
+// max_ctas > 0 caps the CTAs per query
+bool plan_topk_small(int64_t n, int32_t M, int32_t k, int sms, TopkPlan *plan, int64_t max_ctas = 0);
 int64_t topk_small_workspace_bytes(const TopkPlan &plan, int64_t nq, int32_t k);
 int launch_topk_small(const uint8_t *codes, int64_t n, int32_t M, const uint8_t *luts, int64_t nq, int32_t k,
                       int32_t metric, uint16_t *out_sums, int64_t *out_idx, void *workspace, const TopkPlan &plan,

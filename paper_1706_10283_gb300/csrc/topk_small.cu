@@ -693,10 +693,11 @@ namespace bolt {
 static size_t small_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Fills the small-path fields of plan if this size class applies.
-bool plan_topk_small(int64_t n, int32_t M, int32_t k, int sms, TopkPlan *plan) {
+bool plan_topk_small(int64_t n, int32_t M, int32_t k, int sms, TopkPlan *plan, int64_t max_ctas) {
     const int64_t nb = num_blocks(n);
     if (nb == 0 || sms <= 0 || k > kMaxSmallK) return false;
     int64_t G = sms;
+    if (max_ctas > 0 && G > max_ctas) G = max_ctas;
     if (G > nb) G = nb;
     if (G > kSmallMergeKeys / k) G = kSmallMergeKeys / k;
     if (G > 256) G = 256;  // the merge's exact path takes one list per thread
